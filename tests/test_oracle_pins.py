@@ -1,0 +1,526 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden/paper_constants.txt), exact moment identities,
+isotropy of the interaction weights, textbook special cases (BGK + Guo
+forcing), permutation/conservation invariants and brute-force symmetries.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_12934_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+
+
+def golden():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, val, _cite = [s.strip() for s in line.split("|")]
+        out[key] = val
+    return out
+
+
+def frac_list(s):
+    return [Fraction(t) for t in s.split()]
+
+
+# ---------------------------------------------------------------- lattice
+
+def test_lattice_weights_match_paper_and_isotropy():
+    g = golden()
+    ex, ey, w, opp = O.lattice()
+    assert np.allclose(w, [float(v) for v in frac_list(g["omega"])], rtol=0, atol=1e-16)
+    cs2 = float(Fraction(g["cs2"]))
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert abs((w * ex).sum()) < 1e-16 and abs((w * ey).sum()) < 1e-16
+    assert abs((w * ex * ex).sum() - cs2) < 1e-15
+    assert abs((w * ex * ey).sum()) < 1e-16
+    # fourth-order isotropy of D2Q9: sum w ex^4 = 3 sum w ex^2 ey^2 = 3 cs^4
+    assert abs((w * ex ** 4).sum() - 3 * cs2 ** 2) < 1e-15
+    for i in range(9):
+        assert ex[opp[i]] == -ex[i] and ey[opp[i]] == -ey[i]
+
+
+def test_velocity_order_matches_boundary_sets():
+    g = golden()
+    ex, ey, _, _ = O.lattice()
+    xmin = [int(v) for v in g["unknown_xmin"].split()]
+    ymax = [int(v) for v in g["unknown_ymax"].split()]
+    xmax = [int(v) for v in g["unknown_xmax"].split()]
+    assert sorted(i for i in range(9) if ex[i] > 0) == xmin
+    assert sorted(i for i in range(9) if ey[i] < 0) == ymax
+    assert sorted(i for i in range(9) if ex[i] < 0) == xmax
+    sets = [[int(v) for v in s.split(",")] for s in g["periodic_sets"].split()]
+    assert sorted(i for i in range(9) if ex[i] > 0) == sets[0]
+    assert sorted(i for i in range(9) if ex[i] < 0) == sets[1]
+    assert sorted(i for i in range(9) if ey[i] > 0) == sets[2]
+    assert sorted(i for i in range(9) if ey[i] < 0) == sets[3]
+
+
+# ------------------------------------------------------------ moment matrix
+
+def test_moment_matrix_rows_and_orthogonality():
+    g = golden()
+    T, Ti = O.moment_matrix()
+    for r in range(3):
+        assert np.array_equal(T[r], np.array([float(v) for v in g["T_row%d" % r].split()]))
+    ex, ey, _, _ = O.lattice()
+    # hydrodynamic rows: density, momentum and the two stress moments
+    assert np.array_equal(T[3], ex) and np.array_equal(T[5], ey)
+    assert np.array_equal(T[7], ex * ex - ey * ey) and np.array_equal(T[8], ex * ey)
+    # entries are integers; T T^T is exactly diagonal
+    assert np.array_equal(T, np.round(T))
+    G = T @ T.T
+    assert np.array_equal(G, np.diag([9, 36, 36, 6, 12, 6, 12, 4, 4]).astype(float))
+    assert np.allclose(Ti @ T, np.eye(9), atol=1e-15)
+    assert np.linalg.matrix_rank(T) == 9
+
+
+def test_printed_T_rows_3_to_8_are_singular():
+    """The reading of Eq. 3 replaces printed rows 3-8: as printed, T is singular."""
+    printed = np.array([
+        [1, 1, 1, 1, 1, 1, 1, 1, 1],
+        [-4, -1, -1, -1, -1, 2, 2, 2, 2],
+        [4, -2, -2, -2, -2, 1, 1, 1, 1],
+        [0, 1, 0, -1, 0, 1, -1, 1, 1],
+        [0, -1, 0, 2, 0, 1, -1, 1, -1],
+        [0, 0, 1, 0, -1, 1, -1, -1, -1],
+        [0, 0, -2, 0, 2, 1, -1, -1, 0],
+        [0, 1, -1, 1, -1, 0, 0, 0, 1],
+        [0, 0, 0, 0, 0, 1, 1, 1, 1]], dtype=float)
+    assert np.linalg.matrix_rank(printed) < 9
+
+
+# --------------------------------------------------------- equilibrium, forcing
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_feq_moments(seed):
+    rng = np.random.default_rng(seed)
+    ex, ey, _, _ = O.lattice()
+    for _ in range(20):
+        rho = rng.uniform(0.001, 2.0)
+        ux, uy = rng.uniform(-0.1, 0.1, 2)
+        f = O.feq(rho, ux, uy)
+        assert abs(f.sum() - rho) < 1e-14
+        assert abs((ex * f).sum() - rho * ux) < 1e-15
+        assert abs((ey * f).sum() - rho * uy) < 1e-15
+        assert abs((ex * ex * f).sum() - rho * (1 / 3 + ux * ux)) < 1e-14
+        assert abs((ey * ey * f).sum() - rho * (1 / 3 + uy * uy)) < 1e-14
+        assert abs((ex * ey * f).sum() - rho * ux * uy) < 1e-15
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_forcing_moments(seed):
+    rng = np.random.default_rng(seed)
+    ex, ey, _, _ = O.lattice()
+    for _ in range(20):
+        ux, uy, Fx, Fy = rng.uniform(-0.1, 0.1, 4)
+        fb = O.fbar(ux, uy, Fx, Fy)
+        assert abs(fb.sum()) < 1e-16
+        assert abs((ex * fb).sum() - Fx) < 1e-16
+        assert abs((ey * fb).sum() - Fy) < 1e-16
+        assert abs((ex * ex * fb).sum() - 2 * ux * Fx) < 1e-16
+        assert abs((ey * ey * fb).sum() - 2 * uy * Fy) < 1e-16
+        assert abs((ex * ey * fb).sum() - (ux * Fy + uy * Fx)) < 1e-16
+
+
+# ---------------------------------------------------------------- collision
+
+def test_collision_reduces_to_bgk_guo():
+    """With S = I / tau the MRT operator of Eq. 1 is BGK with Guo forcing:
+    f* = f - (f - feq)/tau + (1 - 1/(2 tau)) Fbar (textbook special case)."""
+    rng = np.random.default_rng(5)
+    ex, ey, w, _ = O.lattice()
+    for tau in (0.55, 0.8, 1.0, 1.7):
+        for _ in range(10):
+            rho = rng.uniform(0.1, 1.5)
+            u = rng.uniform(-0.05, 0.05, 2)
+            F = rng.uniform(-0.01, 0.01, 2)
+            f = O.feq(rho, *u) + rng.uniform(-0.01, 0.01, 9) * w
+            s = np.full(9, 1.0 / tau)
+            got = O.collide(f, rho, u[0], u[1], F[0], F[1], s)
+            # Guo forcing term written out from its textbook form
+            eu = ex * u[0] + ey * u[1]
+            guo = w * (3 * ((ex - u[0]) * F[0] + (ey - u[1]) * F[1]) + 9 * eu * (ex * F[0] + ey * F[1]))
+            uu = u @ u
+            fe = w * rho * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * uu)
+            want = f - (f - fe) / tau + (1 - 0.5 / tau) * guo
+            assert np.max(np.abs(got - want)) < 1e-15
+
+
+def test_collision_conservation_and_fixed_point():
+    rng = np.random.default_rng(7)
+    ex, ey, w, _ = O.lattice()
+    s = np.array([1.0, 1.3, 1.1, 1.0, 1.2, 1.0, 1.2, 1.6, 1.6])
+    for _ in range(50):
+        rho = rng.uniform(0.01, 1.5)
+        u = rng.uniform(-0.05, 0.05, 2)
+        F = rng.uniform(-0.01, 0.01, 2)
+        f = O.feq(rho, *u) + rng.uniform(-0.02, 0.02, 9) * w * rho
+        rho = f.sum()  # the step passes rho_k = sum_i f_i (Eq. 8)
+        fs = O.collide(f, rho, u[0], u[1], F[0], F[1], s)
+        assert abs(fs.sum() - f.sum()) < 1e-15
+        # s_j = 1: the post-collision momentum is rho u + F/2
+        assert abs((ex * fs).sum() - (rho * u[0] + 0.5 * F[0])) < 1e-15
+        assert abs((ey * fs).sum() - (rho * u[1] + 0.5 * F[1])) < 1e-15
+        # equilibrium without force is a fixed point
+        fe = O.feq(rho, *u)
+        assert np.max(np.abs(O.collide(fe, rho, u[0], u[1], 0, 0, s) - fe)) < 1e-16
+
+
+def test_relaxation_rates_follow_eq5_and_eq26():
+    g = golden()
+    nu = float(g["nu_eq26"])
+    S26 = [float(v) for v in g["S_eq26"].split()]
+    w = W.laplace(nx=8, ny=8, R=2, nu=(nu, nu))
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u)
+    s = o.scalars()["s"]
+    for k in range(2):
+        assert s[k][0] == 1.0 and s[k][3] == 1.0 and s[k][5] == 1.0  # s_rho = s_j = 1
+        assert round(s[k][7], 2) == S26[7] and round(s[k][8], 2) == S26[8]
+        assert round(s[k][2], 2) == S26[2] and round(s[k][1], 2) == S26[1]
+        assert s[k][6] == S26[6] == s[k][4]
+        # Eq. 5 inverted back
+        assert abs((1 / s[k][7] - 0.5) / 3 - nu) < 1e-15
+
+
+def test_s_eps_from_most_viscous_phase():
+    w = W.laplace(nx=8, ny=8, R=2, nu=(0.02, 0.3))
+    adj = O.Oracle2D(w.cfg, w.solid, w.rho, w.u).scalars()["s"]
+    cfg0 = dict(w.cfg, s_eps_mode=0)
+    own = O.Oracle2D(cfg0, w.solid, w.rho, w.u).scalars()["s"]
+    seps = 1 / (3 * 0.3 + 0.5)
+    assert abs(adj[0][2] - seps) < 1e-15 and abs(adj[1][2] - seps) < 1e-15
+    assert abs(own[0][2] - 1 / (3 * 0.02 + 0.5)) < 1e-15
+    assert abs(own[1][2] - seps) < 1e-15
+
+
+# ----------------------------------------------------- interaction stencil
+
+def test_stencil_weights_match_paper_and_isotropy():
+    g = golden()
+    wmap = {int(a): Fraction(b) for a, b in (t.split(":") for t in g["w8"].split())}
+    dx, dy, w = O.stencil()
+    assert len(dx) == 24
+    vecs = set(zip(dx.tolist(), dy.tolist()))
+    assert len(vecs) == 24 and (0, 0) not in vecs
+    fw = []
+    for a, b, c in zip(dx, dy, w):
+        r2 = int(a * a + b * b)
+        assert r2 in wmap and abs(c - float(wmap[r2])) < 1e-17
+        fw.append((int(a), int(b), wmap[r2]))
+
+    def mom(px, py):
+        return sum(W_ * Fraction(a) ** px * Fraction(b) ** py for a, b, W_ in fw)
+
+    assert mom(2, 0) == 1 and mom(1, 1) == 0 and mom(0, 2) == 1  # E2 = identity
+    assert mom(4, 0) == 3 * mom(2, 2)                            # E4 isotropic
+    assert mom(6, 0) == 5 * mom(4, 2)                            # E6: 15 : 3
+    assert mom(8, 0) * 9 == 105 * mom(4, 4) and mom(6, 2) * 9 == 15 * mom(4, 4)  # E8
+    for px in range(0, 9):
+        for py in range(0, 9 - px):
+            if (px + py) % 2 == 1:
+                assert mom(px, py) == 0
+
+
+def _box(nx, ny, periodic, G12=1.0, Gw=(0.0, 0.0), solid=None):
+    rho = np.ones((2, ny, nx)) * 0.5
+    cfg = W._base_cfg(nx, ny, periodic, G12, Gw, (0.1, 0.1))
+    return O.Oracle2D(cfg, solid, rho)
+
+
+def test_force_of_linear_and_quadratic_field_is_exact_gradient():
+    nx, ny = 16, 14
+    o = _box(nx, ny, (0, 0), G12=0.7)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    psi = np.empty((2, ny, nx))
+    psi[0] = 0.3 + 0.01 * x - 0.02 * y
+    psi[1] = 0.5 + 0.003 * x * x + 0.002 * x * y - 0.001 * y * y + 0.01 * y
+    F = o.eval_forces(psi)
+    gx1 = 0.006 * x + 0.002 * y
+    gy1 = 0.002 * x - 0.002 * y + 0.01
+    sl = (slice(2, ny - 2), slice(2, nx - 2))
+    assert np.max(np.abs(F[0, 0][sl] - (-0.7 * psi[0] * gx1)[sl])) < 1e-15
+    assert np.max(np.abs(F[0, 1][sl] - (-0.7 * psi[0] * gy1)[sl])) < 1e-15
+    assert np.max(np.abs(F[1, 0][sl] - (-0.7 * psi[1] * 0.01)[sl])) < 1e-15
+    assert np.max(np.abs(F[1, 1][sl] - (-0.7 * psi[1] * -0.02)[sl])) < 1e-15
+
+
+def test_fluid_fluid_forces_cancel_on_periodic_domain():
+    nx, ny = 13, 11
+    o = _box(nx, ny, (1, 1), G12=2.3)
+    psi = np.random.default_rng(3).uniform(0.0, 1.0, (2, ny, nx))
+    F = o.eval_forces(psi)
+    tot = F[0] + F[1]
+    assert abs(tot[0].sum()) < 1e-13 and abs(tot[1].sum()) < 1e-13
+
+
+def test_adhesion_is_local_and_repulsive_for_positive_gw():
+    nx, ny = 12, 12
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[0, :] = 1
+    o = _box(nx, ny, (1, 0), G12=0.0, Gw=(0.4, -0.4), solid=solid)
+    psi = np.ones((2, ny, nx)) * 0.5
+    psi[:, solid != 0] = 0
+    F = o.eval_forces(psi)
+    # top edge is closed and counts as solid too: check only the lower half
+    assert np.all(np.abs(F[:, :, 3:6, :]) < 1e-17)        # > 2 nodes from any solid
+    assert np.all(np.abs(F[:, 0, 1:3, :]) < 1e-16)        # no tangential push on a flat wall
+    assert np.all(F[0, 1, 1:3, :] > 0) and np.all(F[1, 1, 1:3, :] < 0)
+    assert np.allclose(F[0, 1, 1:3, :], -F[1, 1, 1:3, :], atol=1e-17)
+
+
+# --------------------------------------------------- streaming / boundaries
+
+def _collisionless(nx, ny, periodic, solid=None, seed=0):
+    rng = np.random.default_rng(seed)
+    cfg = W._base_cfg(nx, ny, periodic, 0.0, (0.0, 0.0), (0.1, 0.1))
+    cfg["s_full"] = np.zeros((2, 9))
+    rho = np.ones((2, ny, nx))
+    if solid is not None:
+        rho[:, solid != 0] = 0
+    o = O.Oracle2D(cfg, solid, rho)
+    f = rng.uniform(0.0, 1.0, (2, 9, ny, nx))
+    if solid is not None:
+        f[:, :, solid != 0] = 0
+    o.set_f(f)
+    return o, f
+
+
+def test_periodic_streaming_is_a_shift_and_returns_after_L_steps():
+    nx, ny = 7, 6
+    o, f0 = _collisionless(nx, ny, (1, 1))
+    ex, ey, _, _ = O.lattice()
+    o.step(1)
+    f1 = o.f()
+    for i in range(9):
+        assert np.array_equal(f1[:, i], np.roll(np.roll(f0[:, i], ey[i], axis=1), ex[i], axis=2))
+    o.step(nx * ny - 1)  # lcm of the periods divides nx*ny
+    assert np.array_equal(o.f(), f0)
+
+
+def test_halfway_bounce_back_reverses_and_conserves_mass():
+    nx, ny = 9, 8
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[3, 4] = 1
+    solid[5, 1:3] = 1
+    o, f0 = _collisionless(nx, ny, (0, 0), solid=solid, seed=4)
+    _, _, _, opp = O.lattice()
+    m0 = o.scalars()["mass"].copy()
+    o.step(1)
+    f1 = o.f()
+    # node (2,3) sits left of the solid (3,4)? use node (3,3): its +x neighbour is solid
+    y, x = 3, 3
+    assert f1[0, 3, y, x] == f0[0, 1, y, x]  # population 1 hit the wall and came back as 3
+    o.step(300)
+    m1 = o.scalars()["mass"]
+    assert np.all(np.abs(m1 - m0) / m0 < 1e-13)
+
+
+def test_uniform_flow_is_a_fixed_point():
+    nx, ny = 8, 7
+    cfg = W._base_cfg(nx, ny, (1, 1), 0.9, (0.0, 0.0), (0.05, 0.3))
+    rho = np.empty((2, ny, nx))
+    rho[0] = 0.4
+    rho[1] = 0.7
+    u = np.zeros((2, ny, nx))
+    u[0] = 0.03
+    u[1] = -0.01
+    o = O.Oracle2D(cfg, None, rho, u)
+    o.step(20)
+    r, uu, _ = o.macros()
+    assert np.max(np.abs(r - rho)) < 1e-14
+    assert np.max(np.abs(uu - u)) < 1e-15
+
+
+# ------------------------------------------------------ whole-step invariants
+
+def test_periodic_laplace_conserves_mass_and_momentum():
+    w = W.laplace(nx=40, ny=40, R=10)
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u, threads=4)
+    ex, ey, _, _ = O.lattice()
+    m0 = o.scalars()["mass"].copy()
+    o.step(400)
+    m1 = o.scalars()["mass"]
+    assert np.all(np.abs(m1 - m0) / m0 < 1e-12)
+    f = o.f()
+    px = (f * ex[None, :, None, None]).sum()
+    py = (f * ey[None, :, None, None]).sum()
+    # zero net interaction force: total momentum stays at its initial value (0)
+    assert abs(px) < 1e-10 and abs(py) < 1e-10
+
+
+def test_label_swap_symmetry():
+    rng = np.random.default_rng(11)
+    nx, ny = 24, 18
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[0] = solid[-1] = 1
+    cfg = W._base_cfg(nx, ny, (1, 0), 1.4, (0.3, -0.2), (0.05, 0.2), body=(1e-5, 0))
+    rho = rng.uniform(0.1, 1.0, (2, ny, nx))
+    rho[:, solid != 0] = 0
+    a = O.Oracle2D(cfg, solid, rho)
+    cfg2 = dict(cfg, Gw=(-0.2, 0.3), nu=(0.2, 0.05))
+    b = O.Oracle2D(cfg2, solid, rho[::-1].copy())
+    a.step(50)
+    b.step(50)
+    ra, ua, _ = a.macros()
+    rb, ub, _ = b.macros()
+    assert np.max(np.abs(ra - rb[::-1])) < 1e-13
+    assert np.max(np.abs(ua - ub)) < 1e-13
+
+
+def test_mirror_symmetric_channel_stays_symmetric():
+    w = W.channel(nx=48, ny=20, R=5, xc=14, yc=9.5, u_max=0.02, G12=1.6)
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u)
+    o.step(60)
+    rho, u, _ = o.macros()
+    assert np.max(np.abs(rho - rho[:, ::-1, :])) < 1e-12
+    assert np.max(np.abs(u[0] - u[0, ::-1, :])) < 1e-12
+    assert np.max(np.abs(u[1] + u[1, ::-1, :])) < 1e-12
+
+
+# ------------------------------------------------------------ open boundaries
+
+def _small_channel(alpha=True, chi=True, droplet=True):
+    return W.channel(nx=60, ny=22, R=6, xc=20, u_max=0.02, G12=1.6, alpha=alpha, chi=chi,
+                     droplet=droplet)
+
+
+def test_inlet_alpha_restores_prescribed_momentum():
+    """Eqs. 15-19 as read: after the correction, every inlet node's
+    momentum sum_i e_i f_i + F_k/2 equals rho_in,k u_in exactly."""
+    w = _small_channel()
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u)
+    o.step(30)
+    ex, ey, _, _ = O.lattice()
+    fp = o.fpost()
+    Fp = o.force_prev()
+    face = w.cfg["faces"][0]
+    for k in range(2):
+        for j in range(face["lo"], face["hi"] + 1):
+            mx = (ex * fp[k, :, j, 0]).sum() + 0.5 * Fp[k, 0, j, 0]
+            my = (ey * fp[k, :, j, 0]).sum() + 0.5 * Fp[k, 1, j, 0]
+            tx = face["rho_in"][k] * face["profile"][j - face["lo"]]
+            assert abs(mx - tx) < 1e-15 and abs(my) < 1e-15
+
+
+def test_inlet_without_alpha_misses_prescribed_momentum():
+    w = _small_channel(alpha=False)
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u)
+    o.step(30)
+    ex, _, _, _ = O.lattice()
+    fp = o.fpost()
+    Fp = o.force_prev()
+    face = w.cfg["faces"][0]
+    err = max(abs((ex * fp[1, :, j, 0]).sum() + 0.5 * Fp[1, 0, j, 0]
+                  - face["rho_in"][1] * face["profile"][j - 1]) for j in range(1, 21))
+    assert err > 1e-6
+
+
+def test_single_phase_channel_reaches_flux_balance():
+    """With the chi correction the outlet mass flux matches the inlet flux
+    at steady state (Eq. 23 -> chi -> 1) and the mass drift falls well below
+    that of the uncorrected outflow scheme.  Q is built from node momenta,
+    which differ from the link fluxes across the column planes by a
+    gradient term at the boundary columns, so chi settles within 1 % of one
+    and a residual drift remains (the paper reports a mass deviation of a
+    few per cent with the correction, Sec. III B)."""
+    rate = {}
+    for chi in (1, 0):
+        w = W.channel(nx=40, ny=14, u_max=0.02, G12=0.0, Gw=(0, 0), nu=(1 / 6, 1 / 6),
+                      droplet=False, chi=chi)
+        o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u, threads=4)
+        o.step(4000)
+        s = o.scalars()
+        if chi:
+            assert abs(s["chi"] - 1.0) < 1e-2
+            assert abs(s["Qin"] - s["Qout"]) / abs(s["Qin"]) < 1e-2
+        m0 = s["mass"].sum()
+        o.step(2000)
+        rate[chi] = abs(o.scalars()["mass"].sum() - m0) / m0
+    assert rate[1] < 0.5 * rate[0]
+
+
+def test_outlet_mass_drift_smaller_with_chi():
+    """Mass drift with the chi correction stays below the uncorrected
+    outflow scheme (paper, Sec. III B/III C, Figs. 5c, 8b)."""
+    drift = {}
+    for chi in (True, False):
+        w = W.channel(nx=80, ny=22, R=6, xc=50, u_max=0.03, G12=1.2, Gw=(0.0, 0.0),
+                      nu=(1 / 6, 1 / 6), chi=chi)
+        o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u, threads=4)
+        m0 = o.scalars()["mass"].sum()
+        dev = []
+        for _ in range(30):
+            o.step(100)
+            dev.append(abs(o.scalars()["mass"].sum() - m0) / m0)
+        drift[chi] = max(dev)
+    assert drift[True] < 0.25 * drift[False]
+
+
+# ----------------------------------------------------------- physics pins
+
+def _layered_profile(mu, yc, L, Fb):
+    """Steady layered channel flow with walls at y = +-L and a body force:
+    mu(y) du/dy = -Fb y, i.e. u(y) = Fb * int_|y|^L s / mu(s) ds.  With a
+    sharp interface and constant densities this is Eq. 27."""
+    ny = len(mu)
+    yn = np.arange(ny) - yc
+    fl = slice(1, ny - 1)
+    ys = np.linspace(-L, L, 40001)
+    g = ys / np.interp(ys, yn[fl], mu[fl])
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (g[1:] + g[:-1]) * np.diff(ys))])
+    return np.interp(yn, ys, Fb * (cum[-1] - cum))
+
+
+@pytest.mark.parametrize("M, Fb, nu2, tol", [(1.0, 1e-6, 1 / 6, 0.02), (5.0, 2e-6, 1 / 30, 0.03),
+                                             (0.2, 2e-6, 1 / 6, 0.03)])
+def test_two_phase_poiseuille_profile(M, Fb, nu2, tol):
+    """Two-phase Poiseuille flow (Sec. III B, Eq. 27; the paper reports a
+    relative error below 1.52 % for M = 1/20, 1, 20 at L = 50).  Each
+    component relaxes its own stress, so the mixture's dynamic viscosity
+    is mu = rho_1 nu_1 + rho_2 nu_2; the steady profile must match the
+    closed-form integral of the momentum balance for that mu(y).  L = 20
+    here, so the diffuse interfaces take a larger share of the channel."""
+    w = W.poiseuille(M=M, Fb=Fb, half=20, a=10, nu2=nu2, G12=1.2)
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u, threads=4)
+    o.step(30000)
+    rho, u, _ = o.macros()
+    nu1, nu2 = w.cfg["nu"]
+    mu = rho[0, :, 2] * nu1 + rho[1, :, 2] * nu2
+    ua = _layered_profile(mu, w.meta["yc"], w.meta["L"], Fb)
+    sl = slice(1, w.cfg["ny"] - 1)
+    assert np.max(np.abs(u[0, sl, 2] - ua[sl])) / ua.max() < tol
+    assert np.max(np.abs(u[1])) < 1e-12  # no transverse flow
+
+
+def test_laplace_law_linear_in_inverse_radius():
+    """Delta p = gamma / R (Sec. III A): Delta p * R is the same surface
+    tension for every radius, and the fit of Delta p against 1/R passes
+    through the origin."""
+    G = 1.5
+    radii = [10, 13, 16, 19]
+    dps = []
+    for R in radii:
+        w = W.laplace(nx=64, ny=64, R=R, G12=G)
+        o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u, threads=8)
+        o.step(3000)
+        rho, _, _ = o.macros()
+        p = O.pressure(rho, G)
+        dps.append(p[32, 32] - p[0, 0])
+    x = 1.0 / np.array(radii)
+    A = np.vstack([x, np.ones_like(x)]).T
+    (gamma, icpt), res, _, _ = np.linalg.lstsq(A, np.array(dps), rcond=None)
+    pred = A @ np.array([gamma, icpt])
+    r2 = 1 - ((np.array(dps) - pred) ** 2).sum() / ((np.array(dps) - np.mean(dps)) ** 2).sum()
+    assert gamma > 0
+    assert r2 > 0.999
+    assert abs(icpt) < 0.05 * max(dps)
