@@ -1,0 +1,227 @@
+/*
+ * lbm.h - C ABI of the GB300 two-component MRT pseudopotential lattice
+ * Boltzmann solver with the corrected open boundaries of arxiv 2512.12934.
+ *
+ * Conventions (every entry point):
+ *  - Plain C types only; no C++ or framework types cross this boundary.
+ *  - The library owns all device state it allocates.  The caller owns every
+ *    host buffer it passes; the library never keeps a host pointer past the
+ *    call that received it.
+ *  - Fields are row-major with x fastest: a scalar field is [nz][ny][nx]
+ *    (nz = 1 in 2D); a per-component field is [2][nz][ny][nx]; a vector
+ *    field is [dim][nz][ny][nx] with dim = 2 (D2Q9) or 3 (D3Q19).
+ *  - Work is enqueued on the CUDA stream given at creation (NULL = the
+ *    legacy default stream).  Calls that return data synchronise that
+ *    stream.  No C++ exception crosses the boundary; a numerical failure
+ *    is a status code, never a device trap.
+ *  - One context must not be used from two threads at once; separate
+ *    contexts are independent.
+ *  - A failing call returns a non-zero lbm_status and records a message
+ *    readable with lbm_last_error().
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1, /* rejected before any device work */
+    LBM_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    LBM_ERR_OOM = 3,         /* device or host allocation failed */
+    LBM_ERR_DIVERGED = 4,    /* a non-finite density or velocity appeared */
+    LBM_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    LBM_ERR_UNSUPPORTED = 6, /* valid request this build does not implement */
+    LBM_ERR_IO = 7           /* checkpoint file could not be read/written */
+} lbm_status;
+
+enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+
+/* Arithmetic / storage of the populations.  FP32: f stored and computed in
+ * float.  FP32_FP16STORE: f stored as half deviations from w_i * rho0,
+ * computed in float.  FP64: stored and computed in double (diagnostic). */
+enum { LBM_FP32 = 0, LBM_FP32_FP16STORE = 1, LBM_FP64 = 2 };
+
+enum { LBM_INLET_VELOCITY = 1, LBM_OUTLET_CONVECTIVE = 2 };
+enum { LBM_XMIN = 0, LBM_XMAX = 1, LBM_YMIN = 2, LBM_YMAX = 3, LBM_ZMIN = 4, LBM_ZMAX = 5 };
+
+/* s_eps choice: own viscosity of each component (the uncorrected scheme) or
+ * the largest viscosity of the two phases (Sec. III A of the paper). */
+enum { LBM_SEPS_OWN_NU = 0, LBM_SEPS_MAX_NU = 1 };
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
+
+/* Lattice and grid.  nz = 1 for D2Q9.  Every non-periodic extent must be
+ * >= 5 (the interaction stencil of Eq. 10 reaches two nodes). */
+typedef struct {
+    int lattice;     /* LBM_D2Q9 or LBM_D3Q19 */
+    int nx, ny, nz;
+    int periodic[3]; /* non-zero: that axis wraps (App. B, Eq. B2) */
+} lbm_grid;
+
+/* Physical parameters (Sec. II A).
+ *  G12        fluid-fluid strength of Eq. 10 (weights as printed).
+ *  Gw[k]      adhesion strength of Eq. 11 for component k (constant).
+ *  nu[k]      kinematic viscosity; s_nu,k = 1/(3 nu_k + 1/2) (Eq. 5);
+ *             must give 0 < s_nu,k < 2.
+ *  s_e        rate of the energy moment; <= 0 selects s_e,k = s_nu,k.
+ *  s_q        rate of both heat-flux moments (Eq. 4); <= 0 selects 1.2.
+ *  s_eps_mode LBM_SEPS_MAX_NU (paper) or LBM_SEPS_OWN_NU.
+ *  body_force body-force density, shared between components by rho_k/rho.
+ *  precision  LBM_FP32, LBM_FP32_FP16STORE or LBM_FP64.
+ *  rho0_store reference density of the FP16 deviation storage (<= 0: 1). */
+typedef struct {
+    double G12;
+    double Gw[2];
+    double nu[2];
+    double s_e;
+    double s_q;
+    int s_eps_mode;
+    double body_force[3];
+    int precision;
+    double rho0_store;
+} lbm_params;
+
+/* One open face (Sec. II B).  The face is the whole grid side `side`,
+ * restricted to the inclusive extent [lo, hi] along its tangential axes
+ * (index 0 = the first tangential axis in x, y, z order; index 1 is used in
+ * 3D only).  Solid nodes inside the extent are skipped.
+ *  kind = LBM_INLET_VELOCITY: NEQ extrapolation of the unknown populations
+ *    (Eqs. 13, 14) followed, when alpha_correction != 0, by the alpha
+ *    correction (Eqs. 15-19).  u_profile (host, may be NULL = 0) holds the
+ *    inflow speed along the inward normal at each face position, row-major
+ *    over the extent; rho_in[k] are the prescribed component densities.
+ *  kind = LBM_OUTLET_CONVECTIVE: convective outflow (Eqs. 20, 21); when
+ *    chi_correction != 0 the outlet normal velocity is rescaled by the
+ *    mass-flux ratio chi (Eqs. 22, 23).
+ * At most one outlet face.  The inward neighbour of every face node must be
+ * an ordinary fluid node.  A face may not lie on a periodic axis. */
+typedef struct {
+    int kind;
+    int side;
+    int lo[2], hi[2];
+    const double* u_profile;
+    double rho_in[2];
+    int alpha_correction;
+    int chi_correction;
+} lbm_open_bc;
+
+/* Diagnostics (FP64 reductions on the device).
+ *  mass[k]   sum of rho_k over the fluid nodes (post-collision state);
+ *  lambda    outlet coefficient of Eq. 21 the next step will use;
+ *  chi       outlet correction of Eq. 23 the next step will use;
+ *  q_in      inlet mass flux sum (rho_1+rho_2) u.n_in of the last step;
+ *  q_out     the same at the column x_{N-1} next to the outlet;
+ *  max_speed largest |u^eq| of the last reported macroscopic fields;
+ *  step      number of completed time steps;
+ *  launches  number of kernels this context has launched;
+ *  status    LBM_OK or LBM_ERR_DIVERGED. */
+typedef struct {
+    double mass[2];
+    double lambda, chi, q_in, q_out;
+    double max_speed;
+    int64_t step;
+    int64_t launches;
+    int status;
+} lbm_diag;
+
+/* Create a solver (Sec. II; call stack of one time step below).
+ *  solid     host [nz][ny][nx] bytes, non-zero = solid node; NULL = none.
+ *  rho_init  host [2][nz][ny][nx] initial component densities.
+ *  u_init    host [dim][nz][ny][nx] initial common velocity; NULL = 0.
+ *  cuda_stream  a cudaStream_t (NULL = legacy default stream).
+ * The initial populations are the equilibria of Eq. 6 at (rho_k, u).
+ * Returns LBM_ERR_INVALID_ARG (nothing allocated) for an invalid grid,
+ * rates outside (0, 2), a bad face, or a NULL required pointer. */
+lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params,
+                      const lbm_open_bc* bcs, int nbc, const uint8_t* solid,
+                      const double* rho_init, const double* u_init,
+                      void* cuda_stream, lbm_ctx** out);
+
+/* Restart the context from new initial fields on the same grid, faces and
+ * parameters (host rho_init [2][nz][ny][nx], u_init [dim][nz][ny][nx] or
+ * NULL): populations become the equilibria of Eq. 6, the open-boundary
+ * state is cleared (lambda = 0, chi = 1), the step counter returns to 0. */
+lbm_status lbm_reset(lbm_ctx* ctx, const double* rho_init, const double* u_init);
+
+/* Enqueue nsteps time steps (nsteps >= 0) on the context's stream.  Each
+ * step is one fused launch: pull streaming (Eq. 2) with halfway bounce-back
+ * (Eq. B1) and periodic wrap (Eq. B2); inlet reconstruction (Eqs. 13-19);
+ * convective outlet (Eqs. 20, 21); densities and pseudopotentials with
+ * ghost mirrors (Eqs. 24, 25); forces (Eqs. 10, 11); common velocity
+ * (Eqs. 7, 8) with the outlet rescaled by chi (Eq. 22); MRT collision with
+ * forcing (Eqs. 1, 3-6, 9); and the FP64 flux reductions that give lambda
+ * and chi for the next step (Eqs. 21, 23).  Returns without waiting for the
+ * GPU; launch errors are reported at once, divergence by the next call
+ * that synchronises (lbm_sync, lbm_get_*). */
+lbm_status lbm_step(lbm_ctx* ctx, int64_t nsteps);
+
+/* Wait for the context's stream; LBM_ERR_DIVERGED if a non-finite density
+ * or velocity was produced since creation. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Macroscopic fields used by the most recent collision (after creation:
+ * the initial fields): rho [2][nz][ny][nx] and u^eq [dim][nz][ny][nx], as
+ * float.  dst_is_device != 0: both pointers are device memory on the
+ * context's device (e.g. a torch CUDA tensor's data_ptr); otherwise host.
+ * Solid nodes read 0. */
+lbm_status lbm_get_macros(lbm_ctx* ctx, float* rho, float* u, int dst_is_device);
+
+/* The same fields as double, host memory only. */
+lbm_status lbm_get_macros_f64(lbm_ctx* ctx, double* rho, double* u);
+
+/* Post-collision populations [2][Q][nz][ny][nx] (host, double), Q = 9 or 19,
+ * in the velocity order of the lattice (D2Q9: e_0..e_8 as in Eq. 13/20). */
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f);
+
+/* Overwrite the post-collision populations (host, double, same layout). */
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f);
+
+/* FP64 diagnostics; synchronises. */
+lbm_status lbm_get_diagnostics(lbm_ctx* ctx, lbm_diag* out);
+
+/* Checkpoint: populations, open-boundary state, lambda, chi and the step
+ * counter, so that n steps = k steps + save + load + (n-k) steps bit for bit. */
+lbm_status lbm_save(lbm_ctx* ctx, const char* path);
+lbm_status lbm_load(lbm_ctx* ctx, const char* path);
+
+/* Kernel timing.  every > 0: from now on every `every`-th step kernel is
+ * launched on its own between a pair of CUDA events recorded on the
+ * context's stream (at most 4096 samples are kept); every = 0 turns
+ * sampling off.  Either call clears the samples.  lbm_kernel_time
+ * synchronises and returns the mean device duration of the sampled step
+ * launches in milliseconds and how many were sampled. */
+lbm_status lbm_enable_kernel_timing(lbm_ctx* ctx, int every);
+lbm_status lbm_kernel_time(lbm_ctx* ctx, double* mean_ms, int64_t* samples);
+
+/* Tile shape of the fused step kernel: variant in [0, lbm_num_tile_variants()),
+ * 0: 32x8, 1: 32x4, 2: 64x4, 3: 32x16 nodes per CTA (default 3).  Results do
+ * not depend on the variant; only speed does. */
+lbm_status lbm_set_tile_variant(lbm_ctx* ctx, int variant);
+int lbm_num_tile_variants(void);
+
+/* Step-replay mode: use_graphs != 0 (the default) replays runs of steps
+ * from captured CUDA graphs (two launches per graph node pair, captured on
+ * first use); 0 launches every step individually.  Results are identical. */
+lbm_status lbm_set_graph_mode(lbm_ctx* ctx, int use_graphs);
+
+/* Release all device memory of the context.  NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last failure on ctx (ctx == NULL: the calling thread's last
+ * failure outside a context, e.g. in lbm_create).  Never NULL. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Library version string. */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,1012 @@
+// Host runtime behind the C ABI of include/lbm.h: parameter validation,
+// per-node descriptors, device allocation, the step loop over the fused
+// kernel, FP64 diagnostics and checkpoints.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_thread_err = "";
+
+constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+constexpr int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+constexpr double kW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                          1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+double host_feq(int i, double rho, double ux, double uy) {
+    const double eu = kEx[i] * ux + kEy[i] * uy;
+    const double uu = ux * ux + uy * uy;
+    return kW[i] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+}
+
+void side_normal(int side, int* ox, int* oy) {
+    *ox = side == 0 ? -1 : (side == 1 ? 1 : 0);
+    *oy = side == 2 ? -1 : (side == 3 ? 1 : 0);
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_grid grid{};
+    lbm_params params{};
+    int nx = 0, ny = 0, pitch = 0;
+    int plane = 0;
+    int precision = LBM_FP32;
+    size_t sbytes = 4;  // bytes per stored population
+    size_t rbytes = 4;  // bytes per arithmetic value (aux + macro buffers)
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    void* f[2] = {nullptr, nullptr};
+    uint16_t* info = nullptr;
+    int* blocks = nullptr;          // tile list: fast tiles first, then general tiles
+    uint8_t* block_flags = nullptr;
+    int nfast = 0, ngeneral = 0;
+    void* uin = nullptr;
+    void* Fp[2] = {nullptr, nullptr};
+    void* fo[2] = {nullptr, nullptr};
+    double* scal[2] = {nullptr, nullptr};
+    double* partials = nullptr;
+    int* block_slot = nullptr;
+    unsigned int* counter = nullptr;
+    unsigned int* status = nullptr;
+    void* macro = nullptr;
+    double* diag_partials = nullptr;
+    int diag_blocks = 0;
+    int nslots = 0;
+    int nfaces = 0;
+    FaceDev faces[MAX_FACES]{};
+    int out_face = -1, have_inlet = 0;
+    int open_side[4] = {0, 0, 0, 0};
+    int nface_nodes = 0;
+    int xoff = 0, yoff = 0, variant = 0, tx = 32, ty = 8;
+    dim3 gdim;
+    int cur = 0;
+    int64_t step = 0;
+    int64_t launches = 0;
+    double s[2][9]{};
+    // CUDA-graph replay of step runs: one executable graph per starting parity
+    int use_graphs = 1;
+    cudaStream_t cap_stream = nullptr;
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    // sampled per-launch timing
+    std::vector<int> h_faceid, h_nbrid;  // per node (unpitched): face id + 1, inward-neighbour face id + 1
+    std::vector<uint8_t> host_solid;   // pitched copy of the solid mask
+    std::vector<uint8_t> host_solid_in;  // unpitched mask (re-initialisation)
+    void* stage = nullptr;             // pinned staging buffer for host transfers
+    size_t stage_bytes = 0;
+    int timing_every = 0;
+    std::vector<cudaEvent_t> ev_start, ev_stop;
+    int n_samples = 0;
+    std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_thread_err = msg;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                         \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);           \
+    } while (0)
+
+constexpr int kGraphSteps = 32;  // even: a replay leaves the ping-pong parity unchanged
+constexpr int kMaxSamples = 4096;
+
+void free_ctx(lbm_ctx* c) {
+    if (!c) return;
+    for (int p = 0; p < 2; ++p)
+        if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (cudaEvent_t e : c->ev_start) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
+    void* ptrs[] = {c->f[0], c->f[1], c->info, c->blocks, c->block_flags, c->uin, c->Fp[0], c->Fp[1], c->fo[0], c->fo[1],
+                    c->scal[0], c->scal[1], c->partials, c->block_slot, c->counter, c->status,
+                    c->macro, c->diag_partials};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->stage) cudaFreeHost(c->stage);
+    delete c;
+}
+
+template <typename S, typename R>
+D2Args<S, R> make_args(lbm_ctx* c, bool write_macros) {
+    D2Args<S, R> a{};
+    const int in = c->cur, out = 1 - c->cur;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.pitch = c->pitch;
+    a.plane = c->plane;
+    a.px = c->grid.periodic[0] ? 1 : 0;
+    a.py = c->grid.periodic[1] ? 1 : 0;
+    for (int i = 0; i < 4; ++i) a.open_side[i] = c->open_side[i];
+    a.xoff = c->xoff;
+    a.yoff = c->yoff;
+    a.fin = static_cast<const S*>(c->f[in]);
+    a.fout = static_cast<S*>(c->f[out]);
+    a.info = c->info;
+    a.blocks = c->blocks;
+    a.block_flags = c->block_flags;
+    a.block_slot = c->block_slot;
+    a.list_off = 0;
+    a.nfaces = c->nfaces;
+    for (int i = 0; i < c->nfaces; ++i) a.face[i] = c->faces[i];
+    a.out_face = c->out_face;
+    a.have_inlet = c->have_inlet;
+    a.uin = static_cast<const R*>(c->uin);
+    a.Fp_in = static_cast<const R*>(c->Fp[in]);
+    a.Fp_out = static_cast<R*>(c->Fp[out]);
+    a.fo_in = static_cast<const R*>(c->fo[in]);
+    a.fo_out = static_cast<R*>(c->fo[out]);
+    a.scal_in = c->scal[in];
+    a.scal_out = c->scal[out];
+    a.partials = c->partials;
+    a.counter = c->counter;
+    a.nslots = c->nslots;
+    a.macro = write_macros ? static_cast<R*>(c->macro) : nullptr;
+    a.status = c->status;
+    a.G12 = (R)c->params.G12;
+    a.Gw[0] = (R)c->params.Gw[0];
+    a.Gw[1] = (R)c->params.Gw[1];
+    for (int k = 0; k < 2; ++k)
+        for (int r = 0; r < 9; ++r) a.s[k][r] = (R)c->s[k][r];
+    a.body[0] = (R)c->params.body_force[0];
+    a.body[1] = (R)c->params.body_force[1];
+    a.rho0 = (R)c->params.rho0_store;
+    return a;
+}
+
+// Both tile lists of one step.  side != nullptr: the general list runs on a
+// forked branch (used while capturing graphs).
+template <typename S, typename R>
+cudaError_t launch_lists(lbm_ctx* c, bool macros, cudaStream_t st, cudaStream_t side) {
+    D2Args<S, R> a = make_args<S, R>(c, macros);
+    cudaError_t e = cudaSuccess;
+    const bool fork = side && c->nfast > 0 && c->ngeneral > 0;
+    if (fork) {
+        e = cudaEventRecord(c->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, c->ev_fork, 0);
+    }
+    if (e == cudaSuccess) e = launch_d2q9_step<S, R>(a, c->variant, false, c->nfast, st);
+    a.list_off = c->nfast;
+    if (e == cudaSuccess) e = launch_d2q9_step<S, R>(a, c->variant, true, c->ngeneral, fork ? side : st);
+    if (fork && e == cudaSuccess) {
+        e = cudaEventRecord(c->ev_join, side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join, 0);
+    }
+    return e;
+}
+
+template <typename S, typename R>
+lbm_status launch_one(lbm_ctx* c, bool macros, cudaStream_t st) {
+    cudaError_t e = launch_lists<S, R>(c, macros, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "d2q9 step launch");
+    // the ping-pong slot written by this step becomes current
+    c->cur = 1 - c->cur;
+    c->step += 1;
+    c->launches += (c->nfast > 0) + (c->ngeneral > 0);
+    return LBM_OK;
+}
+
+// Capture kGraphSteps consecutive steps that start at ping-pong parity `par`.
+template <typename S, typename R>
+lbm_status ensure_graph(lbm_ctx* c, int par) {
+    if (c->gexec[par]) return LBM_OK;
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    if (!c->side_stream) CK(cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+    if (!c->ev_fork) CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    if (!c->ev_join) CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    const int saved = c->cur;
+    c->cur = par;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) {
+        e = launch_lists<S, R>(c, false, c->cap_stream, c->side_stream);
+        c->cur = 1 - c->cur;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    c->cur = saved;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[par], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec[par] = nullptr;
+        return cuda_fail(c, e, "step graph capture");
+    }
+    return LBM_OK;
+}
+
+// cnt steps without macro output: graph replays, then single launches.
+template <typename S, typename R>
+lbm_status run_plain(lbm_ctx* c, int64_t cnt) {
+    while (c->use_graphs && cnt >= kGraphSteps) {
+        if (ensure_graph<S, R>(c, c->cur) != LBM_OK) {
+            c->use_graphs = 0;  // capture unavailable: keep launching the same kernel directly
+            cudaGetLastError();
+            break;
+        }
+        cudaError_t e = cudaGraphLaunch(c->gexec[c->cur], c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step graph launch");
+        c->step += kGraphSteps;
+        c->launches += (int64_t)kGraphSteps * ((c->nfast > 0) + (c->ngeneral > 0));
+        cnt -= kGraphSteps;
+    }
+    for (; cnt > 0; --cnt) {
+        lbm_status st = launch_one<S, R>(c, false, c->stream);
+        if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
+template <typename S, typename R>
+lbm_status launch_sampled(lbm_ctx* c, bool macros) {
+    const int i = c->n_samples;
+    if ((int)c->ev_start.size() <= i) {
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        c->ev_start.push_back(a);
+        c->ev_stop.push_back(b);
+    }
+    CK(cudaEventRecord(c->ev_start[i], c->stream));
+    lbm_status st = launch_one<S, R>(c, macros, c->stream);
+    if (st != LBM_OK) return st;
+    CK(cudaEventRecord(c->ev_stop[i], c->stream));
+    c->n_samples += 1;
+    return LBM_OK;
+}
+
+template <typename S, typename R>
+lbm_status run_steps(lbm_ctx* c, int64_t n) {
+    auto sampling = [c]() { return c->timing_every > 0 && c->n_samples < kMaxSamples; };
+    int64_t remaining = n;
+    while (remaining > 1) {
+        int64_t chunk = remaining - 1;  // the last step writes the macroscopic fields
+        if (sampling()) {
+            const int64_t until = (c->timing_every - c->step % c->timing_every) % c->timing_every;
+            if (until == 0) {
+                lbm_status st = launch_sampled<S, R>(c, false);
+                if (st != LBM_OK) return st;
+                --remaining;
+                continue;
+            }
+            chunk = std::min(chunk, until);
+        }
+        lbm_status st = run_plain<S, R>(c, chunk);
+        if (st != LBM_OK) return st;
+        remaining -= chunk;
+    }
+    if (sampling() && c->step % c->timing_every == 0) return launch_sampled<S, R>(c, true);
+    return launch_one<S, R>(c, true, c->stream);
+}
+
+// Store/convert helpers for host <-> device population and aux transfers.
+template <typename S>
+S to_store(double v, double wr);
+template <>
+float to_store<float>(double v, double) { return (float)v; }
+template <>
+double to_store<double>(double v, double) { return v; }
+template <>
+__half to_store<__half>(double v, double wr) { return __float2half_rn((float)(v - wr)); }
+
+template <typename S>
+double from_store(S v, double wr);
+template <>
+double from_store<float>(float v, double) { return (double)v; }
+template <>
+double from_store<double>(double v, double) { return v; }
+template <>
+double from_store<__half>(__half v, double wr) { return (double)__half2float(v) + wr; }
+
+template <typename S>
+lbm_status upload_f(lbm_ctx* c, const double* fh, int which) {
+    const size_t count = (size_t)18 * c->plane;
+    CK(cudaStreamSynchronize(c->stream));  // the staging buffer may still feed an earlier copy
+    S* buf = static_cast<S*>(c->stage);
+    std::fill(buf, buf + count, to_store<S>(0.0, 0.0));
+    const double rho0 = c->params.rho0_store;
+    const size_t N = (size_t)c->nx * c->ny;
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < 9; ++i)
+            for (int y = 0; y < c->ny; ++y)
+                for (int x = 0; x < c->nx; ++x) {
+                    const double v = fh[((size_t)k * 9 + i) * N + (size_t)y * c->nx + x];
+                    buf[(size_t)(k * 9 + i) * c->plane + (size_t)y * c->pitch + x] =
+                        to_store<S>(v, kW[i] * rho0);
+                }
+    CK(cudaMemcpyAsync(c->f[which], buf, count * sizeof(S), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status download_f(lbm_ctx* c, double* fh) {
+    const size_t count = (size_t)18 * c->plane;
+    CK(cudaStreamSynchronize(c->stream));
+    const S* buf = static_cast<const S*>(c->stage);
+    CK(cudaMemcpyAsync(c->stage, c->f[c->cur], count * sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double rho0 = c->params.rho0_store;
+    const size_t N = (size_t)c->nx * c->ny;
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < 9; ++i)
+            for (int y = 0; y < c->ny; ++y)
+                for (int x = 0; x < c->nx; ++x) {
+                    const size_t d = (size_t)y * c->pitch + x;
+                    double v = 0.0;
+                    if (!c->host_solid[d])
+                        v = from_store<S>(buf[(size_t)(k * 9 + i) * c->plane + d], kW[i] * rho0);
+                    fh[((size_t)k * 9 + i) * N + (size_t)y * c->nx + x] = v;
+                }
+    return LBM_OK;
+}
+
+lbm_status check_status(lbm_ctx* c) {
+    unsigned int st = 0;
+    CK(cudaMemcpyAsync(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (st) return fail(c, LBM_ERR_DIVERGED, "non-finite density or velocity produced");
+    return LBM_OK;
+}
+
+template <typename R>
+lbm_status copy_macros(lbm_ctx* c, void* rho, void* u, bool to_double, bool dst_dev) {
+    const size_t N = (size_t)c->nx * c->ny;
+    CK(cudaStreamSynchronize(c->stream));
+    const R* buf = static_cast<const R*>(c->stage);
+    CK(cudaMemcpyAsync(c->stage, c->macro, (size_t)4 * c->plane * sizeof(R), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<float> fr, fu;
+    if (!to_double) {
+        fr.resize(2 * N);
+        fu.resize(2 * N);
+    }
+    for (int q = 0; q < 4; ++q)
+        for (int y = 0; y < c->ny; ++y)
+            for (int x = 0; x < c->nx; ++x) {
+                const size_t d = (size_t)y * c->pitch + x;
+                double v = c->host_solid[d] ? 0.0 : (double)buf[(size_t)q * c->plane + d];
+                const size_t h = (size_t)(q & 1) * N + (size_t)y * c->nx + x;
+                if (to_double) {
+                    (q < 2 ? static_cast<double*>(rho) : static_cast<double*>(u))[h] = v;
+                } else {
+                    (q < 2 ? fr : fu)[h] = (float)v;
+                }
+            }
+    if (!to_double) {
+        if (dst_dev) {
+            CK(cudaMemcpyAsync(rho, fr.data(), fr.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(u, fu.data(), fu.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        } else {
+            std::memcpy(rho, fr.data(), fr.size() * sizeof(float));
+            std::memcpy(u, fu.data(), fu.size() * sizeof(float));
+        }
+    }
+    return LBM_OK;
+}
+
+template <typename S, typename R>
+lbm_status init_state(lbm_ctx* c, const double* rho_init, const double* u_init, const uint8_t* solid) {
+    const int nx = c->nx, ny = c->ny;
+    const size_t N = (size_t)nx * ny;
+    std::vector<double> fh((size_t)18 * N, 0.0);
+    std::vector<R> macro((size_t)4 * c->plane, R(0));
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t h = (size_t)y * nx + x;
+            if (solid && solid[h]) continue;
+            const double ux = u_init ? u_init[h] : 0.0, uy = u_init ? u_init[N + h] : 0.0;
+            for (int k = 0; k < 2; ++k)
+                for (int i = 0; i < 9; ++i) fh[((size_t)k * 9 + i) * N + h] = host_feq(i, rho_init[k * N + h], ux, uy);
+            const size_t d = (size_t)y * c->pitch + x;
+            macro[d] = (R)rho_init[h];
+            macro[c->plane + d] = (R)rho_init[N + h];
+            macro[2 * c->plane + d] = (R)ux;
+            macro[3 * c->plane + d] = (R)uy;
+        }
+    lbm_status st = upload_f<S>(c, fh.data(), 0);
+    if (st != LBM_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    std::memcpy(c->stage, macro.data(), macro.size() * sizeof(R));
+    CK(cudaMemcpyAsync(c->macro, c->stage, macro.size() * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    // open-boundary state: outlet populations of the "previous" step are the
+    // initial ones; inlet forces start at zero; lambda = 0, chi = 1
+    std::vector<R> fo((size_t)std::max(1, c->nface_nodes) * 18, R(0));
+    for (int fi = 0; fi < c->nfaces; ++fi) {
+        const FaceDev& F = c->faces[fi];
+        if (F.kind != FACE_OUTLET) continue;
+        for (int t = F.lo; t <= F.hi; ++t) {
+            const int x = F.side == 0 ? 0 : (F.side == 1 ? nx - 1 : t);
+            const int y = F.side == 2 ? 0 : (F.side == 3 ? ny - 1 : t);
+            const size_t h = (size_t)y * nx + x;
+            for (int k = 0; k < 2; ++k)
+                for (int i = 0; i < 9; ++i)
+                    fo[((size_t)(F.base + t - F.lo) * 9 + i) * 2 + k] = (R)fh[((size_t)k * 9 + i) * N + h];
+        }
+    }
+    CK(cudaMemcpy(c->fo[0], fo.data(), fo.size() * sizeof(R), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->fo[1], fo.data(), fo.size() * sizeof(R), cudaMemcpyHostToDevice));
+    const size_t nfn = (size_t)std::max(1, c->nface_nodes);
+    CK(cudaMemset(c->Fp[0], 0, nfn * 8 * sizeof(R)));
+    CK(cudaMemset(c->Fp[1], 0, nfn * 8 * sizeof(R)));
+    CK(cudaMemset(c->status, 0, sizeof(unsigned int)));
+    CK(cudaMemset(c->counter, 0, sizeof(unsigned int)));
+    double sc[8] = {0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    CK(cudaMemcpy(c->scal[0], sc, sizeof(sc), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->scal[1], sc, sizeof(sc), cudaMemcpyHostToDevice));
+    c->cur = 0;
+    c->step = 0;
+    return LBM_OK;
+}
+
+// (Re)build the tile grid and the two tile lists for tile-shape variant v.
+lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
+    if (v < 0 || v >= d2q9_num_variants()) return fail(c, LBM_ERR_INVALID_ARG, "unknown tile variant");
+    if (sync_first) CK(cudaStreamSynchronize(c->stream));
+    const int nx = c->nx, ny = c->ny;
+    const lbm_grid* grid = &c->grid;
+    const std::vector<int>& faceid = c->h_faceid;
+    const std::vector<int>& nbrid = c->h_nbrid;
+    const size_t N = (size_t)nx * ny;
+    std::vector<uint8_t> sol(N);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) sol[(size_t)y * nx + x] = c->host_solid[(size_t)y * c->pitch + x];
+    c->variant = v;
+    c->xoff = c->yoff = 0;
+    c->nslots = 0;
+    // tile grid: keep x_{N-1} and x_N of the outlet in one tile
+    d2q9_variant_tile(c->variant, &c->tx, &c->ty);
+    if (c->out_face >= 0) {
+        const FaceDev& F = c->faces[c->out_face];
+        if (F.side == 1 && nx % c->tx == 1) c->xoff = 1;
+        if (F.side == 3 && ny % c->ty == 1) c->yoff = 1;
+    }
+    c->gdim = dim3((unsigned)((nx + c->xoff + c->tx - 1) / c->tx), (unsigned)((ny + c->yoff + c->ty - 1) / c->ty), 1);
+
+    // Tile lists.  A tile whose psi halo holds an open-face node or crosses an
+    // open side goes to the general list (inlet/outlet reconstruction, ghost
+    // mirror); the rest go to the fast list, flagged EDGE when the pull halo
+    // crosses a grid edge (wrap / closed edge) and SOLID when a solid site can
+    // enter the adhesion stencil.  Tiles of the general list that own inlet
+    // nodes or outlet-neighbour nodes join the flux reduction.
+    std::vector<int> list_fast, list_gen;
+    std::vector<uint8_t> fl_fast, fl_gen;
+    std::vector<int> slots;
+    for (unsigned by = 0; by < c->gdim.y; ++by)
+        for (unsigned bx = 0; bx < c->gdim.x; ++bx) {
+            const int x0 = (int)bx * c->tx - c->xoff, y0 = (int)by * c->ty - c->yoff;
+            const bool edge = x0 - 3 < 0 || x0 + c->tx + 3 > nx || y0 - 3 < 0 || y0 + c->ty + 3 > ny;
+            bool gen = (x0 - 2 < 0 && c->open_side[0]) || (x0 + c->tx + 2 > nx && c->open_side[1]) ||
+                       (y0 - 2 < 0 && c->open_side[2]) || (y0 + c->ty + 2 > ny && c->open_side[3]);
+            bool near_solid = false, part = false;
+            for (int yy = std::max(0, y0 - 2); yy < std::min(ny, y0 + c->ty + 2); ++yy)
+                for (int xx = std::max(0, x0 - 2); xx < std::min(nx, x0 + c->tx + 2); ++xx) {
+                    const size_t h = (size_t)yy * nx + xx;
+                    gen = gen || faceid[h] != 0;
+                    near_solid = near_solid || sol[h] != 0;
+                    const bool own = xx >= x0 && xx < x0 + c->tx && yy >= y0 && yy < y0 + c->ty;
+                    if (own && !sol[h] &&
+                        ((faceid[h] && c->faces[faceid[h] - 1].kind == FACE_INLET) ||
+                         (nbrid[h] && nbrid[h] - 1 == c->out_face)))
+                        part = true;
+                }
+            const bool closed_edge = (x0 - 2 < 0 && !grid->periodic[0]) || (x0 + c->tx + 2 > nx && !grid->periodic[0]) ||
+                                     (y0 - 2 < 0 && !grid->periodic[1]) || (y0 + c->ty + 2 > ny && !grid->periodic[1]);
+            uint8_t fl = 0;
+            if (edge) fl |= BLOCK_EDGE;
+            if (near_solid || closed_edge || gen) fl |= BLOCK_SOLID;
+            const int packed = (int)bx | ((int)by << 16);
+            if (gen) {
+                list_gen.push_back(packed);
+                fl_gen.push_back(fl | BLOCK_GENERAL);
+                slots.push_back(part ? c->nslots++ : -1);
+            } else {
+                list_fast.push_back(packed);
+                fl_fast.push_back(fl);
+            }
+        }
+    c->nfast = (int)list_fast.size();
+    c->ngeneral = (int)list_gen.size();
+    std::vector<int> blist(list_fast);
+    blist.insert(blist.end(), list_gen.begin(), list_gen.end());
+    std::vector<uint8_t> bflags(fl_fast);
+    bflags.insert(bflags.end(), fl_gen.begin(), fl_gen.end());
+    std::vector<int> slot_all((size_t)c->nfast, -1);
+    slot_all.insert(slot_all.end(), slots.begin(), slots.end());
+
+    void* old[] = {c->blocks, c->block_flags, c->block_slot, c->partials};
+    for (void* p : old)
+        if (p) cudaFree(p);
+    c->blocks = nullptr;
+    c->block_flags = nullptr;
+    c->block_slot = nullptr;
+    c->partials = nullptr;
+    for (int p = 0; p < 2; ++p)
+        if (c->gexec[p]) {
+            cudaGraphExecDestroy(c->gexec[p]);
+            c->gexec[p] = nullptr;
+        }
+    CK(cudaMalloc((void**)&c->blocks, blist.size() * sizeof(int) + 4));
+    CK(cudaMalloc((void**)&c->block_flags, bflags.size() + 4));
+    CK(cudaMalloc((void**)&c->block_slot, slot_all.size() * sizeof(int) + 4));
+    CK(cudaMalloc((void**)&c->partials, (size_t)std::max(1, c->nslots) * 4 * 8));
+    CK(cudaMemcpy(c->blocks, blist.data(), blist.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->block_flags, bflags.data(), bflags.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->block_slot, slot_all.data(), slot_all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemset(c->counter, 0, sizeof(unsigned int)));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_version(void) { return "paper_2512_12934_gb300 lbm 0.1 (sm_103a)"; }
+
+const char* lbm_last_error(const lbm_ctx* ctx) {
+    if (ctx) return ctx->err.c_str();
+    return g_thread_err.c_str();
+}
+
+lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_open_bc* bcs, int nbc,
+                      const uint8_t* solid, const double* rho_init, const double* u_init,
+                      void* cuda_stream, lbm_ctx** out) {
+    lbm_ctx* c = nullptr;
+    if (!out) return fail(nullptr, LBM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !params || !rho_init) return fail(nullptr, LBM_ERR_INVALID_ARG, "grid, params and rho_init are required");
+    if (grid->lattice != LBM_D2Q9)
+        return fail(nullptr, LBM_ERR_UNSUPPORTED, "only LBM_D2Q9 is implemented in this build");
+    if (grid->nz != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "D2Q9 needs nz == 1");
+    if (grid->nx < 5 || grid->ny < 5) return fail(nullptr, LBM_ERR_INVALID_ARG, "every extent must be >= 5");
+    if (18LL * ((grid->nx + 31) / 32 * 32) * grid->ny >= (1LL << 31))
+        return fail(nullptr, LBM_ERR_INVALID_ARG, "grid too large: 18 population planes must stay below 2^31 elements");
+    if (params->precision != LBM_FP32 && params->precision != LBM_FP64 &&
+        params->precision != LBM_FP32_FP16STORE)
+        return fail(nullptr, LBM_ERR_INVALID_ARG, "unknown precision");
+    if (nbc < 0 || nbc > MAX_FACES || (nbc > 0 && !bcs))
+        return fail(nullptr, LBM_ERR_INVALID_ARG, "nbc must be in [0, 4] with a bcs array");
+    for (int k = 0; k < 2; ++k)
+        if (!(params->nu[k] > 0.0) || !std::isfinite(params->nu[k]))
+            return fail(nullptr, LBM_ERR_INVALID_ARG, "viscosities must be positive");
+
+    c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    c->grid = *grid;
+    c->params = *params;
+    if (c->params.s_q <= 0.0) c->params.s_q = 1.2;
+    if (c->params.rho0_store <= 0.0) c->params.rho0_store = 1.0;
+    if (c->params.precision != LBM_FP32_FP16STORE) c->params.rho0_store = 0.0;
+    c->nx = grid->nx;
+    c->ny = grid->ny;
+    c->pitch = (grid->nx + 31) / 32 * 32;
+    c->plane = c->pitch * grid->ny;
+    c->precision = params->precision;
+    c->sbytes = params->precision == LBM_FP64 ? 8 : (params->precision == LBM_FP32_FP16STORE ? 2 : 4);
+    c->rbytes = params->precision == LBM_FP64 ? 8 : 4;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+
+    // relaxation rates (Eqs. 4, 5; s_eps from the most viscous phase, Sec. III A)
+    const double numax = std::max(params->nu[0], params->nu[1]);
+    for (int k = 0; k < 2; ++k) {
+        const double snu = 1.0 / (3.0 * params->nu[k] + 0.5);
+        const double seps = params->s_eps_mode == LBM_SEPS_MAX_NU ? 1.0 / (3.0 * numax + 0.5) : snu;
+        const double se = params->s_e > 0.0 ? params->s_e : snu;
+        const double s[9] = {1.0, se, seps, 1.0, c->params.s_q, 1.0, c->params.s_q, snu, snu};
+        for (int r = 0; r < 9; ++r) {
+            if (!(s[r] > 0.0 && s[r] < 2.0)) {
+                free_ctx(c);
+                return fail(nullptr, LBM_ERR_INVALID_ARG, "a relaxation rate falls outside (0, 2)");
+            }
+            c->s[k][r] = s[r];
+        }
+    }
+
+    const int nx = c->nx, ny = c->ny;
+    const size_t N = (size_t)nx * ny;
+    std::vector<uint8_t> sol(N, 0);
+    if (solid)
+        for (size_t i = 0; i < N; ++i) sol[i] = solid[i] ? 1 : 0;
+
+    // open faces
+    std::vector<int> faceid(N, 0), nbrid(N, 0);
+    std::vector<double> uin_h;
+    c->nfaces = nbc;
+    int noutlet = 0;
+    for (int fi = 0; fi < nbc; ++fi) {
+        const lbm_open_bc& b = bcs[fi];
+        FaceDev& F = c->faces[fi];
+        if ((b.kind != LBM_INLET_VELOCITY && b.kind != LBM_OUTLET_CONVECTIVE) || b.side < 0 || b.side > 3) {
+            free_ctx(c);
+            return fail(nullptr, LBM_ERR_INVALID_ARG, "bad face kind or side");
+        }
+        const int along = b.side <= 1 ? ny : nx;
+        if (b.lo[0] < 0 || b.hi[0] >= along || b.lo[0] > b.hi[0]) {
+            free_ctx(c);
+            return fail(nullptr, LBM_ERR_INVALID_ARG, "face extent out of range");
+        }
+        if ((b.side <= 1 && grid->periodic[0]) || (b.side >= 2 && grid->periodic[1])) {
+            free_ctx(c);
+            return fail(nullptr, LBM_ERR_INVALID_ARG, "open face on a periodic axis");
+        }
+        F.kind = b.kind == LBM_INLET_VELOCITY ? FACE_INLET : FACE_OUTLET;
+        F.side = b.side;
+        F.lo = b.lo[0];
+        F.hi = b.hi[0];
+        side_normal(b.side, &F.ox, &F.oy);
+        F.base = c->nface_nodes;
+        F.alpha = b.alpha_correction ? 1 : 0;
+        F.chi = b.chi_correction ? 1 : 0;
+        F.rho_in[0] = b.rho_in[0];
+        F.rho_in[1] = b.rho_in[1];
+        F.sxx = F.syy = 0.0;
+        for (int i = 0; i < 9; ++i)
+            if (kEx[i] * F.ox + kEy[i] * F.oy < 0) {
+                F.sxx += kW[i] * kEx[i] * kEx[i];
+                F.syy += kW[i] * kEy[i] * kEy[i];
+            }
+        if (F.kind == FACE_OUTLET) {
+            ++noutlet;
+            c->out_face = fi;
+        } else {
+            c->have_inlet = 1;
+        }
+        c->open_side[b.side] = 1;
+        const int len = F.hi - F.lo + 1;
+        c->nface_nodes += len;
+        for (int t = 0; t < len; ++t)
+            uin_h.push_back((F.kind == FACE_INLET && b.u_profile) ? b.u_profile[t] : 0.0);
+        for (int t = F.lo; t <= F.hi; ++t) {
+            const int x = b.side == 0 ? 0 : (b.side == 1 ? nx - 1 : t);
+            const int y = b.side == 2 ? 0 : (b.side == 3 ? ny - 1 : t);
+            const size_t h = (size_t)y * nx + x;
+            if (sol[h]) continue;
+            if (faceid[h]) {
+                free_ctx(c);
+                return fail(nullptr, LBM_ERR_INVALID_ARG, "a node lies on two open faces");
+            }
+            faceid[h] = fi + 1;
+        }
+    }
+    if (noutlet > 1) {
+        free_ctx(c);
+        return fail(nullptr, LBM_ERR_INVALID_ARG, "at most one outlet face");
+    }
+    for (int fi = 0; fi < nbc; ++fi) {
+        const FaceDev& F = c->faces[fi];
+        for (int t = F.lo; t <= F.hi; ++t) {
+            const int x = F.side == 0 ? 0 : (F.side == 1 ? nx - 1 : t);
+            const int y = F.side == 2 ? 0 : (F.side == 3 ? ny - 1 : t);
+            if (sol[(size_t)y * nx + x]) continue;
+            const size_t h2 = (size_t)(y - F.oy) * nx + (x - F.ox);
+            if (sol[h2] || faceid[h2] || nbrid[h2]) {
+                free_ctx(c);
+                return fail(nullptr, LBM_ERR_INVALID_ARG, "the inward neighbour of a face node must be plain fluid");
+            }
+            nbrid[h2] = fi + 1;
+        }
+    }
+
+    // per-node descriptors
+    std::vector<uint16_t> info((size_t)c->plane, (uint16_t)INFO_SOLID);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const size_t h = (size_t)y * nx + x;
+            unsigned v = 0;
+            if (sol[h]) {
+                v = INFO_SOLID;
+            } else {
+                for (int i = 0; i < 9; ++i) {
+                    int sx = x - kEx[i], sy = y - kEy[i];
+                    bool blocked = false;
+                    if (sx < 0 || sx >= nx) {
+                        if (grid->periodic[0]) sx = (sx + nx) % nx;
+                        else blocked = true;
+                    }
+                    if (sy < 0 || sy >= ny) {
+                        if (grid->periodic[1]) sy = (sy + ny) % ny;
+                        else blocked = true;
+                    }
+                    if (!blocked && sol[(size_t)sy * nx + sx]) blocked = true;
+                    if (blocked) v |= 1u << i;
+                }
+                v |= (unsigned)faceid[h] << INFO_FACE_SHIFT;
+                v |= (unsigned)nbrid[h] << INFO_NBR_SHIFT;
+            }
+            info[(size_t)y * c->pitch + x] = (uint16_t)v;
+        }
+
+    // device allocation
+    const size_t fbytes = (size_t)18 * c->plane * c->sbytes;
+    const int nfn = std::max(1, c->nface_nodes);
+    c->diag_blocks = 152 * 4;
+    cudaError_t e = cudaGetDevice(&c->device);
+    void** allocs[] = {&c->f[0], &c->f[1], (void**)&c->info, &c->uin, &c->Fp[0], &c->Fp[1], &c->fo[0], &c->fo[1],
+                       (void**)&c->scal[0], (void**)&c->scal[1], (void**)&c->counter, (void**)&c->status, &c->macro, (void**)&c->diag_partials};
+    const size_t sizes[] = {fbytes, fbytes, (size_t)c->plane * 2, (size_t)nfn * c->rbytes,
+                            (size_t)nfn * 8 * c->rbytes, (size_t)nfn * 8 * c->rbytes,
+                            (size_t)nfn * 18 * c->rbytes, (size_t)nfn * 18 * c->rbytes, 64, 64,
+                            16, 16,
+                            (size_t)4 * c->plane * c->rbytes, (size_t)c->diag_blocks * 3 * 8};
+    for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]) && e == cudaSuccess; ++i) {
+        e = cudaMalloc(allocs[i], sizes[i]);
+        if (e == cudaSuccess) e = cudaMemset(*allocs[i], 0, sizes[i]);
+    }
+    if (e != cudaSuccess) {
+        const lbm_status st = e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+        const std::string msg = std::string("device allocation: ") + cudaGetErrorString(e);
+        free_ctx(c);
+        return fail(nullptr, st, msg);
+    }
+    e = cudaMemcpy(c->info, info.data(), info.size() * 2, cudaMemcpyHostToDevice);
+
+    if (e == cudaSuccess && c->nface_nodes > 0) {
+        if (c->rbytes == 8) {
+            e = cudaMemcpy(c->uin, uin_h.data(), uin_h.size() * 8, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> uf(uin_h.begin(), uin_h.end());
+            e = cudaMemcpy(c->uin, uf.data(), uf.size() * 4, cudaMemcpyHostToDevice);
+        }
+    }
+    if (e != cudaSuccess) {
+        const std::string msg = std::string("upload: ") + cudaGetErrorString(e);
+        free_ctx(c);
+        return fail(nullptr, LBM_ERR_CUDA, msg);
+    }
+    c->host_solid.assign((size_t)c->plane, 1);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) c->host_solid[(size_t)y * c->pitch + x] = sol[(size_t)y * nx + x];
+    c->stage_bytes = std::max((size_t)18 * c->plane * c->sbytes, (size_t)4 * c->plane * c->rbytes);
+    e = cudaMallocHost(&c->stage, c->stage_bytes);
+    if (e != cudaSuccess) {
+        c->stage = nullptr;
+        const std::string msg = std::string("pinned staging allocation: ") + cudaGetErrorString(e);
+        free_ctx(c);
+        return fail(nullptr, LBM_ERR_OOM, msg);
+    }
+    c->host_solid_in.assign(sol.begin(), sol.end());
+    c->h_faceid = faceid;
+    c->h_nbrid = nbrid;
+    lbm_status st = build_tiles(c, 3, false);
+    if (st != LBM_OK) {
+        const std::string msg = c->err;
+        free_ctx(c);
+        return fail(nullptr, st, msg);
+    }
+    if (c->precision == LBM_FP64) st = init_state<double, double>(c, rho_init, u_init, solid ? sol.data() : nullptr);
+    else if (c->precision == LBM_FP32) st = init_state<float, float>(c, rho_init, u_init, solid ? sol.data() : nullptr);
+    else st = init_state<__half, float>(c, rho_init, u_init, solid ? sol.data() : nullptr);
+    if (st != LBM_OK) {
+        const std::string msg = c->err;
+        free_ctx(c);
+        return fail(nullptr, st, msg);
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(c, LBM_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return LBM_OK;
+    if (c->precision == LBM_FP64) return run_steps<double, double>(c, nsteps);
+    if (c->precision == LBM_FP32) return run_steps<float, float>(c, nsteps);
+    return run_steps<__half, float>(c, nsteps);
+}
+
+lbm_status lbm_reset(lbm_ctx* c, const double* rho_init, const double* u_init) {
+    if (!c || !rho_init) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    const uint8_t* sol = c->host_solid_in.data();
+    if (c->precision == LBM_FP64) return init_state<double, double>(c, rho_init, u_init, sol);
+    if (c->precision == LBM_FP32) return init_state<float, float>(c, rho_init, u_init, sol);
+    return init_state<__half, float>(c, rho_init, u_init, sol);
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    return check_status(c);
+}
+
+lbm_status lbm_get_macros(lbm_ctx* c, float* rho, float* u, int dst_is_device) {
+    if (!c || !rho || !u) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    lbm_status st = check_status(c);
+    if (st != LBM_OK) return st;
+    if (c->rbytes == 8) return copy_macros<double>(c, rho, u, false, dst_is_device != 0);
+    return copy_macros<float>(c, rho, u, false, dst_is_device != 0);
+}
+
+lbm_status lbm_get_macros_f64(lbm_ctx* c, double* rho, double* u) {
+    if (!c || !rho || !u) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    lbm_status st = check_status(c);
+    if (st != LBM_OK) return st;
+    if (c->rbytes == 8) return copy_macros<double>(c, rho, u, true, false);
+    return copy_macros<float>(c, rho, u, true, false);
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, double* f) {
+    if (!c || !f) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->precision == LBM_FP64) return download_f<double>(c, f);
+    if (c->precision == LBM_FP32) return download_f<float>(c, f);
+    return download_f<__half>(c, f);
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, const double* f) {
+    if (!c || !f) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->precision == LBM_FP64) return upload_f<double>(c, f, c->cur);
+    if (c->precision == LBM_FP32) return upload_f<float>(c, f, c->cur);
+    return upload_f<__half>(c, f, c->cur);
+}
+
+lbm_status lbm_get_diagnostics(lbm_ctx* c, lbm_diag* out) {
+    if (!c || !out) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e;
+    if (c->precision == LBM_FP64)
+        e = launch_d2q9_diag<double, double>((const double*)c->f[c->cur], (const double*)c->macro, c->info, c->nx,
+                                             c->ny, c->pitch, c->plane, 0.0, c->diag_partials, c->diag_blocks, c->stream);
+    else if (c->precision == LBM_FP32)
+        e = launch_d2q9_diag<float, float>((const float*)c->f[c->cur], (const float*)c->macro, c->info, c->nx, c->ny,
+                                           c->pitch, c->plane, 0.0f, c->diag_partials, c->diag_blocks, c->stream);
+    else
+        e = launch_d2q9_diag<__half, float>((const __half*)c->f[c->cur], (const float*)c->macro, c->info, c->nx,
+                                            c->ny, c->pitch, c->plane, (float)c->params.rho0_store,
+                                            c->diag_partials, c->diag_blocks, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "diag launch");
+    c->launches += 1;
+    std::vector<double> part((size_t)c->diag_blocks * 3);
+    double sc[8];
+    unsigned int stw = 0;
+    CK(cudaMemcpyAsync(part.data(), c->diag_partials, part.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(sc, c->scal[c->cur], sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&stw, c->status, sizeof(stw), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double m0 = 0.0, m1 = 0.0, u2 = 0.0;
+    for (int b = 0; b < c->diag_blocks; ++b) {
+        m0 += part[(size_t)b * 3];
+        m1 += part[(size_t)b * 3 + 1];
+        u2 = std::max(u2, part[(size_t)b * 3 + 2]);
+    }
+    out->mass[0] = m0;
+    out->mass[1] = m1;
+    out->lambda = sc[0];
+    out->chi = sc[1];
+    out->q_in = sc[2];
+    out->q_out = sc[3];
+    out->max_speed = std::sqrt(u2);
+    out->step = c->step;
+    out->launches = c->launches;
+    out->status = stw ? LBM_ERR_DIVERGED : LBM_OK;
+    return LBM_OK;
+}
+
+lbm_status lbm_save(lbm_ctx* c, const char* path) {
+    if (!c || !path) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaStreamSynchronize(c->stream));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(c, LBM_ERR_IO, std::string("cannot open ") + path);
+    const size_t fbytes = (size_t)18 * c->plane * c->sbytes;
+    const size_t nfn = (size_t)std::max(1, c->nface_nodes);
+    const size_t mbytes = (size_t)4 * c->plane * c->rbytes;
+    std::vector<char> buf(fbytes + nfn * 8 * c->rbytes + nfn * 18 * c->rbytes + 64 + mbytes);
+    char* p = buf.data();
+    CK(cudaMemcpy(p, c->f[c->cur], fbytes, cudaMemcpyDeviceToHost));
+    p += fbytes;
+    CK(cudaMemcpy(p, c->Fp[c->cur], nfn * 8 * c->rbytes, cudaMemcpyDeviceToHost));
+    p += nfn * 8 * c->rbytes;
+    CK(cudaMemcpy(p, c->fo[c->cur], nfn * 18 * c->rbytes, cudaMemcpyDeviceToHost));
+    p += nfn * 18 * c->rbytes;
+    CK(cudaMemcpy(p, c->scal[c->cur], 64, cudaMemcpyDeviceToHost));
+    p += 64;
+    CK(cudaMemcpy(p, c->macro, mbytes, cudaMemcpyDeviceToHost));
+    const char magic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+    const int64_t hdr[6] = {c->nx, c->ny, c->precision, c->nface_nodes, c->step, (int64_t)buf.size()};
+    bool ok = std::fwrite(magic, 1, 8, fp) == 8 && std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 &&
+              std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(c, LBM_ERR_IO, std::string("write failed: ") + path);
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx* c, const char* path) {
+    if (!c || !path) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(c, LBM_ERR_IO, std::string("cannot open ") + path);
+    char magic[8];
+    int64_t hdr[6];
+    const size_t fbytes = (size_t)18 * c->plane * c->sbytes;
+    const size_t nfn = (size_t)std::max(1, c->nface_nodes);
+    const size_t mbytes = (size_t)4 * c->plane * c->rbytes;
+    const size_t total = fbytes + nfn * 8 * c->rbytes + nfn * 18 * c->rbytes + 64 + mbytes;
+    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "LBMCKPT1", 8) == 0 &&
+              std::fread(hdr, sizeof(hdr), 1, fp) == 1 && hdr[0] == c->nx && hdr[1] == c->ny &&
+              hdr[2] == c->precision && hdr[3] == c->nface_nodes && hdr[5] == (int64_t)total;
+    std::vector<char> buf(total);
+    ok = ok && std::fread(buf.data(), 1, total, fp) == total;
+    std::fclose(fp);
+    if (!ok) return fail(c, LBM_ERR_IO, std::string("not a matching checkpoint: ") + path);
+    CK(cudaStreamSynchronize(c->stream));
+    const char* p = buf.data();
+    CK(cudaMemcpy(c->f[c->cur], p, fbytes, cudaMemcpyHostToDevice));
+    p += fbytes;
+    CK(cudaMemcpy(c->Fp[c->cur], p, nfn * 8 * c->rbytes, cudaMemcpyHostToDevice));
+    p += nfn * 8 * c->rbytes;
+    CK(cudaMemcpy(c->fo[c->cur], p, nfn * 18 * c->rbytes, cudaMemcpyHostToDevice));
+    p += nfn * 18 * c->rbytes;
+    CK(cudaMemcpy(c->scal[c->cur], p, 64, cudaMemcpyHostToDevice));
+    p += 64;
+    CK(cudaMemcpy(c->macro, p, mbytes, cudaMemcpyHostToDevice));
+    c->step = hdr[4];
+    return LBM_OK;
+}
+
+lbm_status lbm_enable_kernel_timing(lbm_ctx* c, int every) {
+    if (!c || every < 0) return fail(c, LBM_ERR_INVALID_ARG, "bad timing request");
+    CK(cudaStreamSynchronize(c->stream));
+    c->timing_every = every;
+    c->n_samples = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_kernel_time(lbm_ctx* c, double* mean_ms, int64_t* samples) {
+    if (!c || !mean_ms || !samples) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaStreamSynchronize(c->stream));
+    double tot = 0.0;
+    for (int i = 0; i < c->n_samples; ++i) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, c->ev_start[i], c->ev_stop[i]));
+        tot += ms;
+    }
+    *samples = c->n_samples;
+    *mean_ms = c->n_samples ? tot / c->n_samples : 0.0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_tile_variant(lbm_ctx* c, int variant) {
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    return build_tiles(c, variant, true);
+}
+
+int lbm_num_tile_variants(void) { return d2q9_num_variants(); }
+
+lbm_status lbm_set_graph_mode(lbm_ctx* c, int use_graphs) {
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    c->use_graphs = use_graphs ? 1 : 0;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_ctx(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,670 @@
+// Fused D2Q9 two-component MRT pseudopotential step for sm_103a.
+//
+// One launch = one time step.  A CTA owns a TX x TY tile of nodes and
+// stages the densities (pseudopotentials psi_k = rho_k) of the tile plus a
+// two-node halo in shared memory, so the 24-point interaction stencil of
+// Eq. 10 reads on-chip data only.  Populations are stored structure-of-
+// arrays f[k][i][y][x] (x fastest, pitched rows), read once by the pull
+// stream and written once after collision.  Stage order inside the kernel:
+//   pull stream (Eq. 2) + halfway bounce-back (Eq. B1) + periodic wrap
+//   (Eq. B2) -> inlet NEQ extrapolation (Eqs. 13, 14) + alpha correction
+//   (Eqs. 15-19) -> convective outlet (Eqs. 20, 21) -> rho_k, psi_k with
+//   ghost mirrors (Eqs. 24, 25) -> F_f (Eq. 10) + F_ads (Eq. 11) -> common
+//   velocity (Eqs. 7, 8), outlet rescaled by chi (Eq. 22) -> MRT collision
+//   with forcing in moment space (Eqs. 1, 3-6, 9) -> store -> FP64 flux
+//   reductions that set lambda and chi for the next step (Eqs. 21, 23).
+#include <cuda_fp16.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+// ---- D2Q9 lattice (velocity order fixed by Eqs. 13, 14, 20 and B2) -------
+__host__ __device__ constexpr int ex_(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey_(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp_(int i) {
+    return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5);
+}
+template <typename R>
+__host__ __device__ constexpr R w_(int i) {
+    return i == 0 ? R(4) / R(9) : (i <= 4 ? R(1) / R(9) : R(1) / R(36));
+}
+
+// 8th-order isotropic interaction weights by |e|^2 (text after Eq. 12).
+template <typename R>
+__host__ __device__ constexpr R w8_(int dx, int dy) {
+    return (dx * dx + dy * dy == 1) ? R(4) / R(21)
+         : (dx * dx + dy * dy == 2) ? R(4) / R(45)
+         : (dx * dx + dy * dy == 4) ? R(1) / R(60)
+         : (dx * dx + dy * dy == 5) ? R(2) / R(315)
+         : (dx * dx + dy * dy == 8) ? R(1) / R(5040)
+                                    : R(0);
+}
+
+// ---- population storage ------------------------------------------------
+template <typename S, typename R>
+struct Pop {
+    static __device__ __forceinline__ R ld(const S* __restrict__ p, int j, R /*wr*/) {
+        return static_cast<R>(__ldg(p + j));
+    }
+    static __device__ __forceinline__ void st(S* __restrict__ p, int j, R v, R /*wr*/) {
+        p[j] = static_cast<S>(v);
+    }
+};
+template <>
+struct Pop<__half, float> {
+    static __device__ __forceinline__ float ld(const __half* __restrict__ p, int j, float wr) {
+        return __half2float(__ldg(p + j)) + wr;
+    }
+    static __device__ __forceinline__ void st(__half* __restrict__ p, int j, float v, float wr) {
+        p[j] = __float2half_rn(v - wr);
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ R feq_(int i, R rho, R ux, R uy) {
+    const R eu = R(ex_(i)) * ux + R(ey_(i)) * uy;
+    const R uu = ux * ux + uy * uy;
+    return w_<R>(i) * rho * (R(1) + R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu);
+}
+
+// ---- pulls -----------------------------------------------------------------
+// Node index n = y * pitch + x (32-bit: the host rejects grids whose 18
+// population planes exceed 2^31 elements).  Pull stream (Eq. 2): f_i(x) =
+// f*_i(x - e_i); a set bit i in `info` means that source is solid or outside
+// a closed edge, and halfway bounce-back (Eq. B1) takes f*_opp(i)(x).
+
+// Interior pull: every source lies inside the grid, no wrap needed.
+template <typename S, typename R>
+__device__ __forceinline__ void pull_interior(const D2Args<S, R>& a, int n, unsigned info, R (&f)[2][9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const bool bb = (info >> i) & 1u;
+        const int src = bb ? n : n - ex_(i) - ey_(i) * a.pitch;
+        const int dir = bb ? opp_(i) : i;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            f[k][i] = Pop<S, R>::ld(a.fin, (k * 9 + dir) * a.plane + src, w_<R>(dir) * a.rho0);
+    }
+}
+
+// General pull: sources wrap on periodic axes.
+template <typename S, typename R>
+__device__ __forceinline__ void pull_wrap(const D2Args<S, R>& a, int x, int y, unsigned info, R (&f)[2][9]) {
+    const int n = y * a.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        int src, dir;
+        if ((info >> i) & 1u) {
+            src = n;
+            dir = opp_(i);
+        } else {
+            int sx = x - ex_(i), sy = y - ey_(i);
+            if (sx < 0) sx += a.nx; else if (sx >= a.nx) sx -= a.nx;
+            if (sy < 0) sy += a.ny; else if (sy >= a.ny) sy -= a.ny;
+            src = sy * a.pitch + sx;
+            dir = i;
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            f[k][i] = Pop<S, R>::ld(a.fin, (k * 9 + dir) * a.plane + src, w_<R>(dir) * a.rho0);
+    }
+}
+
+// rho_k = sum_i f_i (Eq. 8) in a fixed pairwise order.
+template <typename R>
+__device__ __forceinline__ R rho_of(const R (&g)[9]) {
+    return g[0] + (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8])));
+}
+template <typename R>
+__device__ __forceinline__ R jx_of(const R (&g)[9]) {
+    return (g[1] - g[3]) + ((g[5] - g[7]) + (g[8] - g[6]));
+}
+template <typename R>
+__device__ __forceinline__ R jy_of(const R (&g)[9]) {
+    return (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
+}
+
+// Open-face reconstruction of the unknown populations of a face node:
+// inlet Eq. 13/14 + alpha (Eqs. 15-19), outlet Eq. 20 with lambda.
+template <typename S, typename R>
+__device__ __forceinline__ void face_fix(const D2Args<S, R>& a, int x, int y, int fid, R (&f)[2][9]) {
+    const FaceDev& F = a.face[fid];
+    const int slot = F.base + ((F.side <= 1) ? y : x) - F.lo;
+    const int x2 = x - F.ox, y2 = y - F.oy;  // inward neighbour
+    const unsigned info2 = a.info[y2 * a.pitch + x2];
+    R g[2][9];
+    pull_wrap(a, x2, y2, info2, g);
+    if (F.kind == FACE_INLET) {
+        const R* Fp = a.Fp_in + slot * 8;  // [node x1/x2][k][d]
+        const R r20 = rho_of(g[0]), r21 = rho_of(g[1]);
+        const R jx = (jx_of(g[0]) + R(0.5) * Fp[4]) + (jx_of(g[1]) + R(0.5) * Fp[6]);
+        const R jy = (jy_of(g[0]) + R(0.5) * Fp[5]) + (jy_of(g[1]) + R(0.5) * Fp[7]);
+        const R inv2 = R(1) / (r20 + r21);
+        const R u2x = jx * inv2, u2y = jy * inv2;
+        const R sp = a.uin[slot];
+        const R uix = -R(F.ox) * sp, uiy = -R(F.oy) * sp;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const R rin = R(F.rho_in[k]);
+            const R r2 = k == 0 ? r20 : r21;
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                if (ex_(i) * F.ox + ey_(i) * F.oy < 0)  // unknown: points into the domain
+                    f[k][i] = feq_<R>(i, rin, uix, uiy) + (g[k][i] - feq_<R>(i, r2, u2x, u2y));
+            if (F.alpha) {
+                const R mx = jx_of(f[k]) + R(0.5) * Fp[k * 2 + 0];
+                const R my = jy_of(f[k]) + R(0.5) * Fp[k * 2 + 1];
+                const R cx = (rin * uix - mx) / R(F.sxx), cy = (rin * uiy - my) / R(F.syy);
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (ex_(i) * F.ox + ey_(i) * F.oy < 0)
+                        f[k][i] += w_<R>(i) * (R(ex_(i)) * cx + R(ey_(i)) * cy);
+            }
+        }
+    } else {
+        const R lam = R(a.scal_in[0]);
+        const R inv = R(1) / (R(1) + lam);
+        const R* fo = a.fo_in + slot * 18;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            if (ex_(i) * F.ox + ey_(i) * F.oy < 0)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) f[k][i] = (fo[i * 2 + k] + lam * g[k][i]) * inv;
+    }
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void pull_general(const D2Args<S, R>& a, int x, int y, unsigned info, R (&f)[2][9]) {
+    pull_wrap(a, x, y, info, f);
+    const int fid = (int)((info >> INFO_FACE_SHIFT) & 7u);
+    if (fid) face_fix(a, x, y, fid - 1, f);
+}
+
+// Virtual site of the psi stencil: periodic wrap, ghost mirror across an open
+// side (Eqs. 24, 25), or solid outside a closed edge.  Returns true if solid.
+template <typename S, typename R>
+__device__ __forceinline__ bool resolve_site(const D2Args<S, R>& a, int& gx, int& gy) {
+    if (gx < 0 || gx >= a.nx) {
+        if (a.px) {
+            gx %= a.nx;
+            if (gx < 0) gx += a.nx;
+        } else if (a.open_side[gx < 0 ? 0 : 1]) {
+            gx = gx < 0 ? -1 - gx : 2 * a.nx - 1 - gx;
+            gx = min(max(gx, 0), a.nx - 1);
+        } else {
+            return true;
+        }
+    }
+    if (gy < 0 || gy >= a.ny) {
+        if (a.py) {
+            gy %= a.ny;
+            if (gy < 0) gy += a.ny;
+        } else if (a.open_side[gy < 0 ? 2 : 3]) {
+            gy = gy < 0 ? -1 - gy : 2 * a.ny - 1 - gy;
+            gy = min(max(gy, 0), a.ny - 1);
+        } else {
+            return true;
+        }
+    }
+    return false;
+}
+
+// Site of the psi stencil on a tile without open sides: periodic wrap or solid
+// outside a closed edge.  Returns true if solid.
+template <typename S, typename R>
+__device__ __forceinline__ bool resolve_closed(const D2Args<S, R>& a, int& gx, int& gy) {
+    if (gx < 0 || gx >= a.nx) {
+        if (!a.px) return true;
+        gx += gx < 0 ? a.nx : -a.nx;
+    }
+    if (gy < 0 || gy >= a.ny) {
+        if (!a.py) return true;
+        gy += gy < 0 ? a.ny : -a.ny;
+    }
+    return false;
+}
+
+// Tile modes: 0 deep interior, 1 edge (wrap / closed edges), 2 general.
+// Density pair of a halo site (no populations kept).  Returns false if solid.
+template <typename S, typename R, int MODE>
+__device__ __forceinline__ bool site_rho(const D2Args<S, R>& a, int gx, int gy, R& r0, R& r1) {
+    if (MODE == 2) {
+        if (resolve_site(a, gx, gy)) return false;
+        const unsigned inf = a.info[gy * a.pitch + gx];
+        if (inf & INFO_SOLID) return false;
+        R g[2][9];
+        pull_general(a, gx, gy, inf, g);
+        r0 = rho_of(g[0]);
+        r1 = rho_of(g[1]);
+    } else if (MODE == 1) {
+        if (resolve_closed(a, gx, gy)) return false;
+        const unsigned inf = a.info[gy * a.pitch + gx];
+        if (inf & INFO_SOLID) return false;
+        R g[2][9];
+        pull_wrap(a, gx, gy, inf, g);
+        r0 = rho_of(g[0]);
+        r1 = rho_of(g[1]);
+    } else {
+        const int n = gy * a.pitch + gx;
+        const unsigned inf = a.info[n];
+        if (inf & INFO_SOLID) return false;
+        R g[2][9];
+        pull_interior(a, n, inf, g);
+        r0 = rho_of(g[0]);
+        r1 = rho_of(g[1]);
+    }
+    return true;
+}
+
+template <typename S, typename R, int TX, int TY>
+struct TileSmem {
+    R rho[2][TY + 4][TX + 4];
+    unsigned char sol[TY + 4][TX + 4];
+    R un[TX > TY ? TX : TY];
+    double red[TX * TY / 32][4];
+};
+
+// Stage the tile's densities (own node + two-node halo) in shared memory;
+// the own node's post-stream populations stay in registers.
+template <typename S, typename R, int TX, int TY, int MODE>
+__device__ __forceinline__ void stage_tile(const D2Args<S, R>& a, TileSmem<S, R, TX, TY>& sm, int x0, int y0,
+                                           int tx, int ty, R (&f)[2][9], unsigned& info, bool& fluid) {
+    constexpr int RX = TX + 4, RY = TY + 4, NT = TX * TY;
+    const int x = x0 + tx, y = y0 + ty;
+    R r0 = R(0), r1 = R(0);
+    unsigned char sol = 1;
+    if (MODE != 0) {
+        const bool inb = (x >= 0 && x < a.nx && y >= 0 && y < a.ny);
+        info = INFO_SOLID;
+        fluid = false;
+        if (inb) {
+            info = a.info[y * a.pitch + x];
+            fluid = !(info & INFO_SOLID);
+            if (fluid) {
+                if (MODE == 2) pull_general(a, x, y, info, f);
+                else pull_wrap(a, x, y, info, f);
+                r0 = rho_of(f[0]);
+                r1 = rho_of(f[1]);
+                sol = 0;
+            }
+        } else if (site_rho<S, R, MODE>(a, x, y, r0, r1)) {
+            sol = 0;
+        }
+    } else {
+        const int n = y * a.pitch + x;
+        info = a.info[n];
+        fluid = !(info & INFO_SOLID);
+        if (fluid) {
+            pull_interior(a, n, info, f);
+            r0 = rho_of(f[0]);
+            r1 = rho_of(f[1]);
+            sol = 0;
+        }
+    }
+    sm.rho[0][ty + 2][tx + 2] = r0;
+    sm.rho[1][ty + 2][tx + 2] = r1;
+    sm.sol[ty + 2][tx + 2] = sol;
+    // halo ring: densities only
+    constexpr int RING = RX * RY - TX * TY;
+    for (int p = threadIdx.x; p < RING; p += NT) {
+        int rx, ry;
+        if (p < 2 * RX) {                // two rows above
+            ry = p / RX;
+            rx = p % RX;
+        } else if (p < 4 * RX) {         // two rows below
+            ry = TY + 2 + (p - 2 * RX) / RX;
+            rx = (p - 2 * RX) % RX;
+        } else {                          // two columns on each side
+            const int q = p - 4 * RX;
+            ry = 2 + q / 4;
+            const int c = q % 4;
+            rx = c < 2 ? c : TX + c;
+        }
+        R h0 = R(0), h1 = R(0);
+        const bool ok = site_rho<S, R, MODE>(a, x0 - 2 + rx, y0 - 2 + ry, h0, h1);
+        sm.rho[0][ry][rx] = h0;
+        sm.rho[1][ry][rx] = h1;
+        sm.sol[ry][rx] = ok ? 0 : 1;
+    }
+}
+
+template <typename S, typename R, int TX, int TY, bool GEN>
+__global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
+    constexpr int NT = TX * TY, NW = NT / 32;
+    __shared__ TileSmem<S, R, TX, TY> sm;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int li = a.list_off + blockIdx.x;
+    const int bxy = a.blocks[li];
+    const unsigned bflags = a.block_flags[li];
+    const int x0 = (bxy & 0xffff) * TX - a.xoff, y0 = (bxy >> 16) * TY - a.yoff;
+    const int x = x0 + tx, y = y0 + ty;
+
+    R f[2][9];
+    unsigned info;
+    bool fluid;
+    if (GEN) stage_tile<S, R, TX, TY, 2>(a, sm, x0, y0, tx, ty, f, info, fluid);
+    else if (bflags & BLOCK_EDGE) stage_tile<S, R, TX, TY, 1>(a, sm, x0, y0, tx, ty, f, info, fluid);
+    else stage_tile<S, R, TX, TY, 0>(a, sm, x0, y0, tx, ty, f, info, fluid);
+    __syncthreads();
+
+    const R rho0 = sm.rho[0][ty + 2][tx + 2], rho1 = sm.rho[1][ty + 2][tx + 2];
+    R Fx0 = R(0), Fy0 = R(0), Fx1 = R(0), Fy1 = R(0);
+    R ux = R(0), uy = R(0);
+    const int own_face = (int)((info >> INFO_FACE_SHIFT) & 7u) - 1;
+    const int nbr_face = (int)((info >> INFO_NBR_SHIFT) & 7u) - 1;
+    if (fluid) {
+        // ---- Eq. 10: 24-point 8th-order gradient of the other component ----
+        R g0x = R(0), g0y = R(0), g1x = R(0), g1y = R(0);
+#pragma unroll
+        for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+            for (int dx = -2; dx <= 2; ++dx) {
+                if (dx * dx + dy * dy == 0 || dx * dx + dy * dy > 8) continue;
+                const R w = w8_<R>(dx, dy);
+                const R p0 = sm.rho[0][ty + 2 + dy][tx + 2 + dx];
+                const R p1 = sm.rho[1][ty + 2 + dy][tx + 2 + dx];
+                if (dx != 0) {
+                    g0x += (w * R(dx)) * p0;
+                    g1x += (w * R(dx)) * p1;
+                }
+                if (dy != 0) {
+                    g0y += (w * R(dy)) * p0;
+                    g1y += (w * R(dy)) * p1;
+                }
+            }
+        // ---- Eq. 11: adhesion, only in tiles that see a solid site ----
+        R ax = R(0), ay = R(0);
+        if (bflags & BLOCK_SOLID) {
+#pragma unroll
+            for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+                for (int dx = -2; dx <= 2; ++dx) {
+                    if (dx * dx + dy * dy == 0 || dx * dx + dy * dy > 8) continue;
+                    const R sv = R(sm.sol[ty + 2 + dy][tx + 2 + dx]);
+                    if (dx != 0) ax += (w8_<R>(dx, dy) * R(dx)) * sv;
+                    if (dy != 0) ay += (w8_<R>(dx, dy) * R(dy)) * sv;
+                }
+        }
+        const R rt = rho0 + rho1;
+        const R inv_rt = R(1) / rt;
+        Fx0 = -a.G12 * rho0 * g1x - a.Gw[0] * rho0 * ax + a.body[0] * rho0 * inv_rt;
+        Fy0 = -a.G12 * rho0 * g1y - a.Gw[0] * rho0 * ay + a.body[1] * rho0 * inv_rt;
+        Fx1 = -a.G12 * rho1 * g0x - a.Gw[1] * rho1 * ax + a.body[0] * rho1 * inv_rt;
+        Fy1 = -a.G12 * rho1 * g0y - a.Gw[1] * rho1 * ay + a.body[1] * rho1 * inv_rt;
+        // ---- Eqs. 7, 8: common velocity ----
+        const R jx = (jx_of(f[0]) + R(0.5) * Fx0) + (jx_of(f[1]) + R(0.5) * Fx1);
+        const R jy = (jy_of(f[0]) + R(0.5) * Fy0) + (jy_of(f[1]) + R(0.5) * Fy1);
+        ux = jx * inv_rt;
+        uy = jy * inv_rt;
+    }
+
+    // ---- Eq. 22: outlet normal velocity = chi * u_n(x_{N-1}), same row ----
+    if (GEN && a.out_face >= 0) {
+        const FaceDev& OF = a.face[a.out_face];
+        bool covers;
+        if (OF.side == 0) covers = (x0 <= 0);
+        else if (OF.side == 1) covers = (x0 + TX > a.nx - 1);
+        else if (OF.side == 2) covers = (y0 <= 0);
+        else covers = (y0 + TY > a.ny - 1);
+        if (covers && OF.chi) {
+            const int along = (OF.side <= 1) ? ty : tx;
+            if (fluid && nbr_face == a.out_face) sm.un[along] = (OF.side <= 1) ? ux : uy;
+            __syncthreads();
+            if (fluid && own_face == a.out_face) {
+                const R chi = R(a.scal_in[1]);
+                if (OF.side <= 1) ux = chi * sm.un[along];
+                else uy = chi * sm.un[along];
+            }
+        }
+    }
+
+    if (fluid) {
+        const int n = y * a.pitch + x;
+        // open-boundary state for the next step (inlet forces, outlet populations)
+        if (GEN && own_face >= 0) {
+            const FaceDev& F = a.face[own_face];
+            const int slot = F.base + ((F.side <= 1) ? y : x) - F.lo;
+            if (F.kind == FACE_INLET) {
+                R* Fp = a.Fp_out + slot * 8;
+                Fp[0] = Fx0; Fp[1] = Fy0; Fp[2] = Fx1; Fp[3] = Fy1;
+            } else {
+                R* fo = a.fo_out + slot * 18;
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (ex_(i) * F.ox + ey_(i) * F.oy < 0) {
+                        fo[i * 2 + 0] = f[0][i];
+                        fo[i * 2 + 1] = f[1][i];
+                    }
+            }
+        }
+        if (nbr_face >= 0 && a.face[nbr_face].kind == FACE_INLET) {
+            const FaceDev& F = a.face[nbr_face];
+            R* Fp = a.Fp_out + (F.base + ((F.side <= 1) ? y : x) - F.lo) * 8 + 4;
+            Fp[0] = Fx0; Fp[1] = Fy0; Fp[2] = Fx1; Fp[3] = Fy1;
+        }
+        if (a.macro) {
+            a.macro[n] = rho0;
+            a.macro[a.plane + n] = rho1;
+            a.macro[2 * a.plane + n] = ux;
+            a.macro[3 * a.plane + n] = uy;
+        }
+        // ---- Eq. 1 in moment space (T of Eq. 3, S of Eq. 4), delta form ----
+        const R uu3 = R(3) * (ux * ux + uy * uy);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const R* s = a.s[k];
+            const R r = k == 0 ? rho0 : rho1;
+            const R fx = k == 0 ? Fx0 : Fx1, fy = k == 0 ? Fy0 : Fy1;
+            const R* g = f[k];
+            const R d13 = g[1] - g[3], d24 = g[2] - g[4], d57 = g[5] - g[7], d86 = g[8] - g[6];
+            const R a13 = g[1] + g[3], a24 = g[2] + g[4], a57 = g[5] + g[7], a68 = g[6] + g[8];
+            const R sa = a13 + a24, sd = a57 + a68;
+            const R me = (R(2) * sd - sa) - R(4) * g[0];
+            const R mp = (sd - R(2) * sa) + R(4) * g[0];
+            const R mjx = d13 + (d57 + d86), mqx = (d57 + d86) - R(2) * d13;
+            const R mjy = d24 + (d57 - d86), mqy = (d57 - d86) - R(2) * d24;
+            const R mxx = a13 - a24, mxy = a57 - a68;
+            const R uF = ux * fx + uy * fy;
+            // post-collision moment increments: -s (m - m_eq) + (1 - s/2) F_m
+            const R de = -s[1] * (me - r * (uu3 - R(2))) + (R(1) - R(0.5) * s[1]) * (R(6) * uF);
+            const R dp = -s[2] * (mp - r * (R(1) - uu3)) + (R(1) - R(0.5) * s[2]) * (R(-6) * uF);
+            const R djx = -s[3] * (mjx - r * ux) + (R(1) - R(0.5) * s[3]) * fx;
+            const R dqx = -s[4] * (mqx + r * ux) - (R(1) - R(0.5) * s[4]) * fx;
+            const R djy = -s[5] * (mjy - r * uy) + (R(1) - R(0.5) * s[5]) * fy;
+            const R dqy = -s[6] * (mqy + r * uy) - (R(1) - R(0.5) * s[6]) * fy;
+            const R dxx = -s[7] * (mxx - r * (ux * ux - uy * uy)) +
+                          (R(1) - R(0.5) * s[7]) * (R(2) * (ux * fx - uy * fy));
+            const R dxy = -s[8] * (mxy - r * ux * uy) + (R(1) - R(0.5) * s[8]) * (ux * fy + uy * fx);
+            // back-transform T^-1 = T^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+            const R ce = de * R(1.0 / 36.0), cp = dp * R(1.0 / 36.0);
+            const R cjx = djx * R(1.0 / 6.0), cqx = dqx * R(1.0 / 12.0);
+            const R cjy = djy * R(1.0 / 6.0), cqy = dqy * R(1.0 / 12.0);
+            const R cxx = dxx * R(0.25), cxy = dxy * R(0.25);
+            const R ax_ = -ce - R(2) * cp, dg = R(2) * ce + cp;
+            const R bx = cjx - R(2) * cqx, by = cjy - R(2) * cqy;
+            const R px = cjx + cqx, py = cjy + cqy;
+            R o[9];
+            o[0] = g[0] + (R(4) * (cp - ce));
+            o[1] = g[1] + (ax_ + bx + cxx);
+            o[2] = g[2] + (ax_ + by - cxx);
+            o[3] = g[3] + (ax_ - bx + cxx);
+            o[4] = g[4] + (ax_ - by - cxx);
+            o[5] = g[5] + (dg + px + py + cxy);
+            o[6] = g[6] + (dg - px + py - cxy);
+            o[7] = g[7] + (dg - px - py + cxy);
+            o[8] = g[8] + (dg + px - py - cxy);
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o[i], w_<R>(i) * a.rho0);
+        }
+    }
+
+    // ---- divergence flag: one atomic per warp at most ----
+    {
+        const bool bad = fluid && !isfinite(rho0 + rho1 + ux + uy);
+        const unsigned m = __ballot_sync(0xffffffffu, bad);
+        if (m && (tid & 31) == 0) atomicOr(a.status, 1u);
+    }
+
+    // ---- FP64 flux reductions for lambda (Eq. 21) and chi (Eq. 23) ----
+    if (GEN && a.nslots > 0) {
+        const int slot = a.block_slot[li];
+        if (slot >= 0) {
+            double v[4] = {0.0, 0.0, 0.0, 0.0};
+            if (fluid && own_face >= 0 && a.face[own_face].kind == FACE_INLET) {
+                const FaceDev& F = a.face[own_face];
+                v[0] = (double)(rho0 + rho1) * (double)(-(R(F.ox) * ux + R(F.oy) * uy));
+            }
+            if (fluid && nbr_face >= 0 && nbr_face == a.out_face) {
+                const FaceDev& F = a.face[nbr_face];
+                const double un = (double)(R(F.ox) * ux + R(F.oy) * uy);
+                v[1] = (double)(rho0 + rho1) * un;
+                v[2] = un;
+                v[3] = 1.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+            if ((tid & 31) == 0)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) sm.red[tid >> 5][j] = v[j];
+            __syncthreads();
+            if (tid == 0) {
+                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int wgrp = 0; wgrp < NW; ++wgrp)
+                    for (int j = 0; j < 4; ++j) acc[j] += sm.red[wgrp][j];
+                for (int j = 0; j < 4; ++j) a.partials[slot * 4 + j] = acc[j];
+                __threadfence();
+                const unsigned done = atomicAdd(a.counter, 1u);
+                if (done == (unsigned)(a.nslots - 1)) {
+                    __threadfence();
+                    double tot[4] = {0.0, 0.0, 0.0, 0.0};
+                    const volatile double* pp = a.partials;
+                    for (int sl = 0; sl < a.nslots; ++sl)
+                        for (int j = 0; j < 4; ++j) tot[j] += pp[sl * 4 + j];
+                    double lam = a.scal_in[0], chi = a.scal_in[1], um = 0.0;
+                    if (a.out_face >= 0 && tot[3] > 0.0) {
+                        um = tot[2] / tot[3];
+                        lam = um > 0.0 ? um : 0.0;
+                        chi = (!a.have_inlet || fabs(tot[1]) < 1e-14) ? 1.0 : tot[0] / tot[1];
+                    }
+                    a.scal_out[0] = lam;
+                    a.scal_out[1] = chi;
+                    a.scal_out[2] = tot[0];
+                    a.scal_out[3] = tot[1];
+                    a.scal_out[4] = um;
+                    *a.counter = 0u;
+                }
+            }
+        }
+    }
+}
+
+// FP64 mass / speed reduction for diagnostics.
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) d2q9_diag_kernel(const S* __restrict__ f, const R* __restrict__ macro,
+                                                        const uint16_t* __restrict__ info, int nx, int ny,
+                                                        int pitch, long long plane, R rho0,
+                                                        double* partials) {
+    double m0 = 0.0, m1 = 0.0, umax = 0.0;
+    const long long total = (long long)nx * ny;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % nx), y = (int)(t / nx);
+        const long long n = (long long)y * pitch + x;
+        if (info[n] & INFO_SOLID) continue;
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            a0 += (double)Pop<S, R>::ld(f, (int)(i * plane + n), w_<R>(i) * rho0);
+            a1 += (double)Pop<S, R>::ld(f, (int)((9 + i) * plane + n), w_<R>(i) * rho0);
+        }
+        m0 += a0;
+        m1 += a1;
+        const double ux = (double)macro[2 * plane + n], uy = (double)macro[3 * plane + n];
+        umax = fmax(umax, ux * ux + uy * uy);
+    }
+    __shared__ double red[3][8];
+    for (int o = 16; o > 0; o >>= 1) {
+        m0 += __shfl_down_sync(0xffffffffu, m0, o);
+        m1 += __shfl_down_sync(0xffffffffu, m1, o);
+        umax = fmax(umax, __shfl_down_sync(0xffffffffu, umax, o));
+    }
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][wid] = m0;
+        red[1][wid] = m1;
+        red[2][wid] = umax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            a0 += red[0][w];
+            a1 += red[1][w];
+            a2 = fmax(a2, red[2][w]);
+        }
+        partials[blockIdx.x * 3 + 0] = a0;
+        partials[blockIdx.x * 3 + 1] = a1;
+        partials[blockIdx.x * 3 + 2] = a2;
+    }
+}
+
+}  // namespace
+
+struct TileShape { int tx, ty; };
+static const TileShape kVariants[] = {{32, 8}, {32, 4}, {64, 4}, {32, 16}};
+
+void d2q9_variant_tile(int variant, int* tx, int* ty) {
+    *tx = kVariants[variant].tx;
+    *ty = kVariants[variant].ty;
+}
+int d2q9_num_variants() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
+
+template <typename S, typename R, int TX, int TY>
+static void launch_tile(const D2Args<S, R>& a, bool general, int nblocks, cudaStream_t st) {
+    if (general) d2q9_step_kernel<S, R, TX, TY, true><<<nblocks, TX * TY, 0, st>>>(a);
+    else d2q9_step_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(a);
+}
+
+template <typename S, typename R>
+cudaError_t launch_d2q9_step(const D2Args<S, R>& a, int variant, bool general, int nblocks, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    switch (variant) {
+    case 0: launch_tile<S, R, 32, 8>(a, general, nblocks, st); break;
+    case 1: launch_tile<S, R, 32, 4>(a, general, nblocks, st); break;
+    case 2: launch_tile<S, R, 64, 4>(a, general, nblocks, st); break;
+    case 3: launch_tile<S, R, 32, 16>(a, general, nblocks, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S, typename R>
+cudaError_t launch_d2q9_diag(const S* f, const R* macro, const uint16_t* info, int nx, int ny,
+                             int pitch, long long plane, R rho0, double* partials, int nblocks,
+                             cudaStream_t st) {
+    d2q9_diag_kernel<S, R><<<nblocks, 256, 0, st>>>(f, macro, info, nx, ny, pitch, plane, rho0, partials);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_d2q9_step<float, float>(const D2Args<float, float>&, int, bool, int, cudaStream_t);
+template cudaError_t launch_d2q9_step<double, double>(const D2Args<double, double>&, int, bool, int, cudaStream_t);
+template cudaError_t launch_d2q9_step<__half, float>(const D2Args<__half, float>&, int, bool, int, cudaStream_t);
+template cudaError_t launch_d2q9_diag<float, float>(const float*, const float*, const uint16_t*, int, int, int,
+                                                    long long, float, double*, int, cudaStream_t);
+template cudaError_t launch_d2q9_diag<double, double>(const double*, const double*, const uint16_t*, int, int,
+                                                      int, long long, double, double*, int, cudaStream_t);
+template cudaError_t launch_d2q9_diag<__half, float>(const __half*, const float*, const uint16_t*, int, int, int,
+                                                     long long, float, double*, int, cudaStream_t);
+
+}  // namespace lbm

@@ -1,0 +1,103 @@
+// Internal declarations shared by the host runtime (lbm_api.cu) and the
+// D2Q9 kernels (lbm_d2q9.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+// Per-node descriptor word (uint16, same pitched layout as one population
+// plane):
+//   bits 0..8   direction i's pull source x - e_i is solid or outside a
+//               non-periodic edge -> halfway bounce-back (Eq. B1); open-face
+//               unknowns also carry the bit and are then rebuilt
+//   bit  9      the node itself is solid
+//   bits 10..12 face id + 1 when the node lies on an open face
+//   bits 13..15 face id + 1 when the node is that face's inward neighbour
+//               (x2 of an inlet, x_{N-1} of the outlet)
+constexpr unsigned INFO_SOLID = 1u << 9;
+constexpr int INFO_FACE_SHIFT = 10;
+constexpr int INFO_NBR_SHIFT = 13;
+constexpr int MAX_FACES = 4;
+
+// Per-tile flags.  Tiles are split into two launch lists: the fast list
+// (deep-interior and edge tiles) and the general list (tiles whose psi halo
+// holds an open-face node or crosses an open side, which need the inlet /
+// outlet reconstruction and the ghost mirror).
+constexpr unsigned BLOCK_EDGE = 1u;     // pull or psi halo crosses a grid edge: wrap / closed-edge logic
+constexpr unsigned BLOCK_SOLID = 2u;    // a solid site lies within the tile's psi halo: adhesion
+constexpr unsigned BLOCK_GENERAL = 4u;  // general list
+
+constexpr int FACE_INLET = 1;
+constexpr int FACE_OUTLET = 2;
+
+// One open face as the kernels see it.
+struct FaceDev {
+    int kind;       // FACE_INLET / FACE_OUTLET
+    int side;       // 0: x=0, 1: x=nx-1, 2: y=0, 3: y=ny-1
+    int lo, hi;     // inclusive extent along the face
+    int ox, oy;     // outward normal
+    int base;       // first slot of this face in the per-face-node arrays
+    int alpha;      // inlet: alpha correction on
+    int chi;        // outlet: chi correction on
+    double rho_in[2];
+    double sxx, syy;  // sum over the unknown set U of w_i e_ix^2 and w_i e_iy^2
+};
+
+// Kernel arguments of one D2Q9 step.  S is the population storage type,
+// R the arithmetic type.
+template <typename S, typename R>
+struct D2Args {
+    int nx, ny, pitch;
+    int plane;              // elements per population plane (pitch * ny); 18 * plane < 2^31
+    int px, py;             // periodic axes
+    int open_side[4];       // 1 if an open face lies on that side (ghost mirror)
+    int xoff, yoff;         // tile-grid origin shift (keeps x_{N-1} with x_N)
+    const S* __restrict__ fin;
+    S* __restrict__ fout;
+    const uint16_t* __restrict__ info;
+    const int* __restrict__ blocks;           // tile list: bx | by << 16
+    const uint8_t* __restrict__ block_flags;  // per list entry: BLOCK_* flags
+    const int* __restrict__ block_slot;       // per list entry: flux-reduction slot or -1
+    int list_off;                             // first list entry of this launch
+    int nfaces;
+    FaceDev face[MAX_FACES];
+    int out_face;           // index of the outlet face or -1
+    int have_inlet;
+    const R* __restrict__ uin;      // [slot] inward normal speed
+    const R* __restrict__ Fp_in;    // [slot][2 nodes][2 comps][2 dims]
+    R* __restrict__ Fp_out;
+    const R* __restrict__ fo_in;    // [slot][9][2] outlet populations of the last step
+    R* __restrict__ fo_out;
+    const double* __restrict__ scal_in;   // [0] lambda, [1] chi
+    double* __restrict__ scal_out;        // lambda, chi, Qin, Qout, Umean
+    double* partials;                     // [slot][4]
+    unsigned int* counter;
+    int nslots;
+    R* __restrict__ macro;                // optional [4][plane]: rho1, rho2, ux, uy
+    unsigned int* status;
+    R G12;
+    R Gw[2];
+    R s[2][9];
+    R body[2];
+    R rho0;                                // FP16 deviation reference density
+};
+
+// Launch one list of tiles of one step: general = false -> fast kernel,
+// true -> general kernel; nblocks list entries starting at a.list_off.
+template <typename S, typename R>
+cudaError_t launch_d2q9_step(const D2Args<S, R>& a, int variant, bool general, int nblocks, cudaStream_t st);
+
+// Tile shape of a kernel variant.
+void d2q9_variant_tile(int variant, int* tx, int* ty);
+int d2q9_num_variants();
+
+// FP64 diagnostics over the current populations and macro buffer:
+// per-block partials [nblocks][3] = mass1, mass2, max |u|^2.
+template <typename S, typename R>
+cudaError_t launch_d2q9_diag(const S* f, const R* macro, const uint16_t* info, int nx, int ny,
+                             int pitch, long long plane, R rho0, double* partials, int nblocks,
+                             cudaStream_t st);
+
+}  // namespace lbm

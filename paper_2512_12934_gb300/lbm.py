@@ -1,0 +1,257 @@
+"""Thin ctypes binding of liblbm.so (include/lbm.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Loading fails loudly when the library is missing; there is
+no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblbm.so")
+
+LBM_OK = 0
+STATUS = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OOM",
+          4: "LBM_ERR_DIVERGED", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_UNSUPPORTED", 7: "LBM_ERR_IO"}
+LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_FP32, LBM_FP32_FP16STORE, LBM_FP64 = 0, 1, 2
+PRECISIONS = {"fp32": LBM_FP32, "fp16store": LBM_FP32_FP16STORE, "fp64": LBM_FP64}
+LBM_INLET_VELOCITY, LBM_OUTLET_CONVECTIVE = 1, 2
+SIDES = {"xmin": 0, "xmax": 1, "ymin": 2, "ymax": 3, "zmin": 4, "zmax": 5}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class lbm_grid(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("periodic", ctypes.c_int * 3)]
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("G12", ctypes.c_double), ("Gw", ctypes.c_double * 2), ("nu", ctypes.c_double * 2),
+                ("s_e", ctypes.c_double), ("s_q", ctypes.c_double), ("s_eps_mode", ctypes.c_int),
+                ("body_force", ctypes.c_double * 3), ("precision", ctypes.c_int),
+                ("rho0_store", ctypes.c_double)]
+
+
+class lbm_open_bc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("side", ctypes.c_int), ("lo", ctypes.c_int * 2),
+                ("hi", ctypes.c_int * 2), ("u_profile", ctypes.POINTER(ctypes.c_double)),
+                ("rho_in", ctypes.c_double * 2), ("alpha_correction", ctypes.c_int),
+                ("chi_correction", ctypes.c_int)]
+
+
+class lbm_diag(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double * 2), ("lambda_", ctypes.c_double), ("chi", ctypes.c_double),
+                ("q_in", ctypes.c_double), ("q_out", ctypes.c_double), ("max_speed", ctypes.c_double),
+                ("step", ctypes.c_int64), ("launches", ctypes.c_int64), ("status", ctypes.c_int)]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+def load():
+    """Load liblbm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    if not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("liblbm.so is missing and could not be built: no CUDA path available")
+    L = ctypes.CDLL(LIB_PATH)
+    c_ctx = ctypes.c_void_p
+    L.lbm_create.restype = ctypes.c_int
+    L.lbm_create.argtypes = [ctypes.POINTER(lbm_grid), ctypes.POINTER(lbm_params), ctypes.POINTER(lbm_open_bc),
+                             ctypes.c_int, ctypes.c_void_p, _dp, _dp, ctypes.c_void_p, ctypes.POINTER(c_ctx)]
+    L.lbm_step.restype = ctypes.c_int
+    L.lbm_step.argtypes = [c_ctx, ctypes.c_int64]
+    L.lbm_reset.restype = ctypes.c_int
+    L.lbm_reset.argtypes = [c_ctx, _dp, _dp]
+    L.lbm_sync.restype = ctypes.c_int
+    L.lbm_sync.argtypes = [c_ctx]
+    L.lbm_get_macros.restype = ctypes.c_int
+    L.lbm_get_macros.argtypes = [c_ctx, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    L.lbm_get_macros_f64.restype = ctypes.c_int
+    L.lbm_get_macros_f64.argtypes = [c_ctx, _dp, _dp]
+    L.lbm_get_populations.restype = ctypes.c_int
+    L.lbm_get_populations.argtypes = [c_ctx, _dp]
+    L.lbm_set_populations.restype = ctypes.c_int
+    L.lbm_set_populations.argtypes = [c_ctx, _dp]
+    L.lbm_get_diagnostics.restype = ctypes.c_int
+    L.lbm_get_diagnostics.argtypes = [c_ctx, ctypes.POINTER(lbm_diag)]
+    L.lbm_save.restype = ctypes.c_int
+    L.lbm_save.argtypes = [c_ctx, ctypes.c_char_p]
+    L.lbm_load.restype = ctypes.c_int
+    L.lbm_load.argtypes = [c_ctx, ctypes.c_char_p]
+    L.lbm_destroy.restype = None
+    L.lbm_destroy.argtypes = [c_ctx]
+    L.lbm_last_error.restype = ctypes.c_char_p
+    L.lbm_last_error.argtypes = [c_ctx]
+    L.lbm_enable_kernel_timing.restype = ctypes.c_int
+    L.lbm_enable_kernel_timing.argtypes = [c_ctx, ctypes.c_int]
+    L.lbm_kernel_time.restype = ctypes.c_int
+    L.lbm_kernel_time.argtypes = [c_ctx, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.lbm_set_tile_variant.restype = ctypes.c_int
+    L.lbm_set_tile_variant.argtypes = [c_ctx, ctypes.c_int]
+    L.lbm_num_tile_variants.restype = ctypes.c_int
+    L.lbm_num_tile_variants.argtypes = []
+    L.lbm_set_graph_mode.restype = ctypes.c_int
+    L.lbm_set_graph_mode.argtypes = [c_ctx, ctypes.c_int]
+    L.lbm_version.restype = ctypes.c_char_p
+    L.lbm_version.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != LBM_OK:
+        msg = load().lbm_last_error(ctx)
+        raise LbmError(status, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+class Solver:
+    """One lbm_ctx built from a plain configuration dictionary (see
+    paper_2512_12934_gb300.workloads for the keys)."""
+
+    def __init__(self, cfg, solid, rho_init, u_init=None, precision="fp32", stream=None, rho0_store=1.0):
+        L = load()
+        nx, ny = cfg["nx"], cfg["ny"]
+        self.nx, self.ny, self.N = nx, ny, nx * ny
+        g = lbm_grid()
+        g.lattice = LBM_D2Q9
+        g.nx, g.ny, g.nz = nx, ny, 1
+        per = cfg.get("periodic", (0, 0))
+        g.periodic[0], g.periodic[1], g.periodic[2] = int(per[0]), int(per[1]), 0
+        p = lbm_params()
+        p.G12 = cfg.get("G12", 0.0)
+        gw = cfg.get("Gw", (0.0, 0.0))
+        p.Gw[0], p.Gw[1] = gw
+        p.nu[0], p.nu[1] = cfg["nu"]
+        p.s_e = cfg.get("s_e", 0.0)
+        p.s_q = cfg.get("s_q", 1.2)
+        p.s_eps_mode = int(cfg.get("s_eps_mode", 1))
+        b = cfg.get("body", (0.0, 0.0))
+        p.body_force[0], p.body_force[1], p.body_force[2] = b[0], b[1], 0.0
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.rho0_store = rho0_store
+        faces = cfg.get("faces", [])
+        BC = (lbm_open_bc * max(1, len(faces)))()
+        keep = []
+        for j, fc in enumerate(faces):
+            BC[j].kind = LBM_INLET_VELOCITY if fc["kind"] == "inlet" else LBM_OUTLET_CONVECTIVE
+            BC[j].side = SIDES[fc["side"]]
+            BC[j].lo[0], BC[j].hi[0] = fc["lo"], fc["hi"]
+            prof = np.ascontiguousarray(fc.get("profile", np.zeros(fc["hi"] - fc["lo"] + 1)), dtype=np.float64)
+            keep.append(prof)
+            BC[j].u_profile = _dptr(prof)
+            r = fc.get("rho_in", (0.0, 0.0))
+            BC[j].rho_in[0], BC[j].rho_in[1] = r
+            BC[j].alpha_correction = int(fc.get("alpha", 1))
+            BC[j].chi_correction = int(fc.get("chi", 1))
+        sol = None
+        if solid is not None:
+            sol = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
+        rho = np.ascontiguousarray(rho_init, dtype=np.float64).reshape(-1)
+        uu = None if u_init is None else np.ascontiguousarray(u_init, dtype=np.float64).reshape(-1)
+        h = ctypes.c_void_p()
+        st = L.lbm_create(ctypes.byref(g), ctypes.byref(p), BC, len(faces),
+                          None if sol is None else sol.ctypes.data_as(ctypes.c_void_p), _dptr(rho),
+                          None if uu is None else _dptr(uu), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        _check(st, None)
+        self.h = h
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, rho_init, u_init=None):
+        rho = np.ascontiguousarray(rho_init, dtype=np.float64).reshape(-1)
+        uu = None if u_init is None else np.ascontiguousarray(u_init, dtype=np.float64).reshape(-1)
+        _check(load().lbm_reset(self.h, _dptr(rho), None if uu is None else _dptr(uu)), self.h)
+
+    def step(self, n=1):
+        _check(load().lbm_step(self.h, int(n)), self.h)
+
+    def sync(self):
+        _check(load().lbm_sync(self.h), self.h)
+
+    def macros(self):
+        """(rho[2][ny][nx], u[2][ny][nx]) as float64 on the host."""
+        rho = np.zeros(2 * self.N)
+        u = np.zeros(2 * self.N)
+        _check(load().lbm_get_macros_f64(self.h, _dptr(rho), _dptr(u)), self.h)
+        return rho.reshape(2, self.ny, self.nx), u.reshape(2, self.ny, self.nx)
+
+    def macros_f32(self, rho_ptr=None, u_ptr=None, device=False):
+        """float32 fields into caller buffers (host numpy arrays, or device
+        pointers when device=True); returns the numpy arrays if none given."""
+        if rho_ptr is None:
+            rho = np.zeros(2 * self.N, dtype=np.float32)
+            u = np.zeros(2 * self.N, dtype=np.float32)
+            _check(load().lbm_get_macros(self.h, rho.ctypes.data, u.ctypes.data, 0), self.h)
+            return rho.reshape(2, self.ny, self.nx), u.reshape(2, self.ny, self.nx)
+        _check(load().lbm_get_macros(self.h, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr), int(device)), self.h)
+        return None
+
+    def populations(self):
+        f = np.zeros(18 * self.N)
+        _check(load().lbm_get_populations(self.h, _dptr(f)), self.h)
+        return f.reshape(2, 9, self.ny, self.nx)
+
+    def set_populations(self, f):
+        a = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        _check(load().lbm_set_populations(self.h, _dptr(a)), self.h)
+
+    def diagnostics(self):
+        d = lbm_diag()
+        _check(load().lbm_get_diagnostics(self.h, ctypes.byref(d)), self.h)
+        return {"mass": np.array(d.mass[:]), "lambda": d.lambda_, "chi": d.chi, "Qin": d.q_in,
+                "Qout": d.q_out, "max_speed": d.max_speed, "step": d.step, "launches": d.launches,
+                "status": d.status}
+
+    def enable_kernel_timing(self, every):
+        _check(load().lbm_enable_kernel_timing(self.h, int(every)), self.h)
+
+    def kernel_time(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(load().lbm_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n)), self.h)
+        return ms.value, n.value
+
+    def set_tile_variant(self, v):
+        _check(load().lbm_set_tile_variant(self.h, int(v)), self.h)
+
+    def set_graph_mode(self, on):
+        _check(load().lbm_set_graph_mode(self.h, int(bool(on))), self.h)
+
+    def save(self, path):
+        _check(load().lbm_save(self.h, path.encode()), self.h)
+
+    def load_checkpoint(self, path):
+        _check(load().lbm_load(self.h, path.encode()), self.h)
+
+
+def version():
+    return load().lbm_version().decode()

@@ -168,3 +168,46 @@ def random_box(nx, ny, seed, periodic=(1, 1), solid_frac=0.0, G12=1.0, Gw=(0.0, 
         rho[:, solid != 0] = 0.0
         u[:, solid != 0] = 0.0
     return Workload("random_%dx%d_s%d" % (nx, ny, seed), cfg, solid, rho, u, 0, {})
+
+
+def tjunction(Wc=40, length_factor=20, Wd=None, side_len=None, x_side=None, Ca=0.01, q_ratio=1.0,
+              M=1.0, G12=1.6, Gw=(0.2, -0.2), u_c=0.01, nu_c=1.0 / 6, seed=2512004) -> Workload:
+    """T-junction droplet generator (Sec. III D): a main channel of width Wc
+    along x (continuous phase, component 2, velocity inlet at x=0, outlet at
+    x=nx-1) and a side channel of width Wd entering from the top (dispersed
+    phase, component 1, velocity inlet on the top face, unknowns 4, 7, 8 of
+    Eq. 14).  Solid walls one node thick.  Ca is recorded for reference; the
+    flow-rate ratio sets the side inflow speed."""
+    Wd = int(Wd if Wd is not None else max(4, Wc // 2))
+    side_len = int(side_len if side_len is not None else 2 * Wc)
+    nx = int(length_factor * Wc)
+    ny = Wc + 2 + side_len
+    x_side = int(x_side if x_side is not None else 4 * Wc)
+    solid = np.ones((ny, nx), dtype=np.uint8)
+    solid[1:Wc + 1, :] = 0                                   # main channel rows 1..Wc
+    solid[Wc + 1:ny, x_side:x_side + Wd] = 0                 # side channel up to the top edge
+    cfg = _base_cfg(nx, ny, (0, 0), G12, Gw, (M * nu_c, nu_c))
+    prof_main = 4.0 * u_c * (np.arange(1, Wc + 1) - 0.5) * (Wc + 0.5 - np.arange(1, Wc + 1)) / (Wc * Wc)
+    q_c = prof_main.sum()
+    xs = np.arange(Wd, dtype=np.float64)
+    prof_side = (xs + 0.5) * (Wd - 0.5 - xs)                 # parabola between the side walls
+    prof_side *= (q_ratio * q_c) / prof_side.sum()           # side flow rate = q_ratio * main flow rate
+    cfg["faces"] = [
+        {"kind": "inlet", "side": "xmin", "lo": 1, "hi": Wc, "rho_in": (FLOOR, 1.0), "alpha": 1, "chi": 0,
+         "profile": prof_main},
+        {"kind": "inlet", "side": "ymax", "lo": x_side, "hi": x_side + Wd - 1, "rho_in": (1.0, FLOOR),
+         "alpha": 1, "chi": 0, "profile": prof_side},
+        {"kind": "outlet", "side": "xmax", "lo": 1, "hi": Wc, "rho_in": (0.0, 0.0), "alpha": 0, "chi": 1,
+         "profile": np.zeros(Wc)},
+    ]
+    rho = np.zeros((2, ny, nx))
+    rho[0] = FLOOR
+    rho[1] = 1.0
+    rho[0, Wc + 1:, :] = 1.0                                 # side channel filled with dispersed phase
+    rho[1, Wc + 1:, :] = FLOOR
+    rho[:, solid != 0] = 0.0
+    u = np.zeros((2, ny, nx))
+    u[0, 1:Wc + 1, :] = prof_main[:, None]
+    u[:, solid != 0] = 0.0
+    return Workload("tjunction_Wc%d" % Wc, cfg, solid, rho, u, 0,
+                    {"Wc": Wc, "Wd": Wd, "x_side": x_side, "Ca": Ca, "q_ratio": q_ratio, "M": M})

@@ -1,0 +1,199 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Bar (stated for the method's FP32 path): after 100 steps the norm-relative
+error max|rho_gpu - rho_ref| / max|rho_ref| and the same for u^eq stay
+<= 1e-5 in FP32.  The FP64 build of the same kernel must agree to 1e-11,
+which shows the two implement the same arithmetic up to rounding order.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_12934_gb300 import lbm
+from paper_2512_12934_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "fp64": 1e-11}
+THREADS = min(16, os.cpu_count() or 1)
+
+
+def rel_inf(a, b):
+    scale = np.max(np.abs(b))
+    return np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0)
+
+
+def both(w, steps, precision):
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u, threads=THREADS)
+    o.step(steps)
+    s = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision=precision)
+    s.step(steps)
+    ro, uo, _ = o.macros()
+    rg, ug = s.macros()
+    return o, s, (ro, uo), (rg, ug)
+
+
+def check(w, steps, precision, tol=None):
+    tol = tol or TOL[precision]
+    o, s, (ro, uo), (rg, ug) = both(w, steps, precision)
+    er, eu = rel_inf(rg, ro), rel_inf(ug, uo)
+    assert np.all(np.isfinite(rg)) and np.all(np.isfinite(ug))
+    assert er <= tol, "rho rel err %.3e" % er
+    assert eu <= tol, "u rel err %.3e" % eu
+    return o, s
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_laplace_config_100x100(precision):
+    """Static droplet, 100x100 periodic, R = 20, G12 = 3.0, nu = 1/6."""
+    check(W.laplace(), 100, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_channel_with_open_boundaries(precision):
+    w = W.channel(nx=200, ny=40, R=8, xc=60, u_max=0.02, G12=1.6, Gw=(0.5, -0.5))
+    o, s = check(w, 100, precision)
+    so, sg = o.scalars(), s.diagnostics()
+    for key in ("lambda", "chi", "Qin", "Qout"):
+        assert abs(sg[key] - so[key]) <= 1e-5 * max(1.0, abs(so[key])), key
+    assert np.allclose(sg["mass"], so["mass"], rtol=1e-6)
+
+
+def test_channel_config_full_size_fp32():
+    """The 1024x128 droplet-migration channel in the launch configuration the
+    benchmark times, 100 steps."""
+    check(W.channel(), 100, "fp32")
+
+
+@pytest.mark.parametrize("nx, ny, seed, solid_frac", [(37, 23, 1, 0.0), (5, 5, 2, 0.0), (33, 9, 3, 0.1),
+                                                      (70, 41, 4, 0.05), (64, 16, 5, 0.0)])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_ragged_periodic_random(nx, ny, seed, solid_frac, precision):
+    w = W.random_box(nx, ny, seed, periodic=(1, 1), solid_frac=solid_frac, G12=0.9, Gw=(0.3, -0.2))
+    check(w, 30, precision)
+
+
+@pytest.mark.parametrize("periodic", [(0, 0), (1, 0), (0, 1)])
+def test_closed_and_mixed_edges(periodic):
+    w = W.random_box(29, 19, 7, periodic=periodic, solid_frac=0.08, G12=0.9, Gw=(0.3, -0.2))
+    check(w, 30, "fp64")
+    check(w, 30, "fp32")
+
+
+@pytest.mark.parametrize("nx", [65, 97, 33])
+def test_outlet_alone_in_last_tile_column(nx):
+    """nx = 1 (mod 32) puts x_{N-1} and x_N in different 32-wide tiles unless
+    the tile grid is shifted; chi needs both in one tile."""
+    w = W.channel(nx=nx, ny=20, R=4, xc=12, u_max=0.02, G12=1.4, Gw=(0.3, -0.3))
+    check(w, 60, "fp64")
+    check(w, 60, "fp32")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_tjunction_two_inlets(precision):
+    w = W.tjunction(Wc=12, length_factor=12, Wd=6, side_len=10, x_side=30, G12=1.2, Gw=(0.1, -0.1))
+    check(w, 100, precision)
+
+
+def test_original_schemes_without_corrections():
+    w = W.channel(nx=120, ny=30, R=6, xc=40, u_max=0.02, G12=1.4, alpha=False, chi=False, s_eps_mode=0)
+    check(w, 100, "fp64")
+    check(w, 100, "fp32")
+
+
+def test_macros_after_create_are_the_initial_fields():
+    w = W.channel(nx=64, ny=20, R=5, xc=20, G12=1.4)
+    s = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision="fp32")
+    rg, ug = s.macros()
+    assert np.max(np.abs(rg - w.rho)) < 1e-6
+    assert np.max(np.abs(ug - w.u)) < 1e-8
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = W.channel(nx=96, ny=24, R=5, xc=30, u_max=0.02, G12=1.4)
+    a = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+    a.step(200)
+    fa = a.populations()
+    b = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+    b.step(100)
+    path = "/tmp/lbm_ckpt_%d.bin" % os.getpid()
+    b.save(path)
+    c = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+    c.load_checkpoint(path)
+    os.remove(path)
+    c.step(100)
+    assert np.array_equal(c.populations(), fa)
+    assert c.diagnostics()["step"] == 200
+
+
+def test_populations_roundtrip_and_oracle_state_injection():
+    """Setting the same populations on both sides and stepping agrees too."""
+    w = W.random_box(40, 24, 9, periodic=(1, 1), G12=0.8)
+    rng = np.random.default_rng(3)
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u)
+    f = o.f() * (1 + 0.01 * rng.uniform(-1, 1, size=o.f().shape))
+    o.set_f(f)
+    s = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision="fp64")
+    s.set_populations(f)
+    assert np.array_equal(s.populations(), f)
+    o.step(20)
+    s.step(20)
+    assert rel_inf(s.macros()[0], o.macros()[0]) < 1e-11
+
+
+def test_divergence_is_reported_as_status():
+    w = W.laplace(nx=32, ny=32, R=8)
+    rho = w.rho.copy()
+    rho[0, 5, 5] = np.nan
+    s = lbm.Solver(w.cfg, w.solid, rho, w.u)
+    s.step(3)
+    with pytest.raises(lbm.LbmError) as e:
+        s.sync()
+    assert e.value.status == 4
+
+
+def test_device_destination_macros():
+    torch = pytest.importorskip("torch")
+    w = W.laplace(nx=48, ny=40, R=10)
+    s = lbm.Solver(w.cfg, w.solid, w.rho, w.u, stream=torch.cuda.current_stream().cuda_stream)
+    s.step(10)
+    rho = torch.empty((2, 40, 48), dtype=torch.float32, device="cuda")
+    u = torch.empty((2, 40, 48), dtype=torch.float32, device="cuda")
+    s.macros_f32(rho.data_ptr(), u.data_ptr(), device=True)
+    rh, uh = s.macros_f32()
+    assert np.array_equal(rho.cpu().numpy(), rh) and np.array_equal(u.cpu().numpy(), uh)
+
+
+def test_repeated_short_calls_equal_one_long_call():
+    w = W.channel(nx=80, ny=20, R=5, xc=25, G12=1.4)
+    a = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+    b = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+    a.step(50)
+    for _ in range(50):
+        b.step(1)
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.macros()[1], b.macros()[1])
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_tile_variants_and_graph_replay_agree(variant):
+    """Tile shape and CUDA-graph replay change the schedule, not the result:
+    on a periodic grid (no reductions) every variant is bit-identical."""
+    w = W.random_box(70, 45, 12, periodic=(1, 1), solid_frac=0.05, G12=0.9, Gw=(0.2, -0.1))
+    a = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+    a.set_tile_variant(variant)
+    a.step(70)
+    b = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+    b.set_graph_mode(0)
+    b.step(70)
+    assert np.array_equal(a.populations(), b.populations())
+    c = W.tjunction(Wc=12, length_factor=12, Wd=6, side_len=10, x_side=30, G12=1.2, Gw=(0.1, -0.1))
+    p = lbm.Solver(c.cfg, c.solid, c.rho, c.u)
+    p.set_tile_variant(variant)
+    p.step(70)
+    q = lbm.Solver(c.cfg, c.solid, c.rho, c.u)
+    q.set_graph_mode(0)
+    q.step(70)
+    assert rel_inf(p.macros()[1], q.macros()[1]) < 1e-6
