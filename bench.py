@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--lbm-steps", type=int, default=5000, help="LBM time steps per benchmark step")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16store", "fp64"])
+    p.add_argument("--workload", default="channel", choices=["channel", "channel_hbm"],
+                   help="channel: the 1024x128 config; channel_hbm: the same physics on 8192x2048")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-hbm", action="store_true")
@@ -209,7 +211,7 @@ def main():
 
     lbm.load()
     stream = torch.cuda.current_stream()
-    w = W.channel()
+    w = W.channel() if args.workload == "channel" else W.channel(nx=8192, ny=2048, R=240, xc=1600)
     S = args.lbm_steps
     solver = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision=args.precision, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -323,7 +325,8 @@ def main():
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": "channel_1024x128_droplet_migration", "grid": [w.cfg["nx"], w.cfg["ny"]],
+            "config": {"workload": "channel_%dx%d_droplet_migration" % (w.cfg["nx"], w.cfg["ny"]),
+                       "grid": [w.cfg["nx"], w.cfg["ny"]],
                        "fluid_nodes": nodes, "lbm_steps_per_step": S, "precision": args.precision,
                        "G12": w.cfg["G12"], "Gw": list(w.cfg["Gw"]), "nu": list(w.cfg["nu"]),
                        "u_max": w.meta["u_max"], "droplet_R": w.meta["R"],

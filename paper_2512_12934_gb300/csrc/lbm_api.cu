@@ -17,8 +17,14 @@
 using namespace lbm;
 
 namespace {
+thread_local char g_thread_err[512] = "";
+}  // namespace
 
-thread_local std::string g_thread_err = "";
+void lbm::set_thread_error(const char* msg) {
+    std::snprintf(g_thread_err, sizeof g_thread_err, "%s", msg ? msg : "");
+}
+
+namespace {
 
 constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 constexpr int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -98,7 +104,7 @@ namespace {
 
 lbm_status fail(lbm_ctx* c, lbm_status st, const std::string& msg) {
     if (c) c->err = msg;
-    else g_thread_err = msg;
+    else lbm::set_thread_error(msg.c_str());
     return st;
 }
 
@@ -574,7 +580,7 @@ const char* lbm_version(void) { return "paper_2512_12934_gb300 lbm 0.1 (sm_103a)
 
 const char* lbm_last_error(const lbm_ctx* ctx) {
     if (ctx) return ctx->err.c_str();
-    return g_thread_err.c_str();
+    return g_thread_err;
 }
 
 lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_open_bc* bcs, int nbc,

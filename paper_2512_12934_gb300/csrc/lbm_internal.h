@@ -100,4 +100,7 @@ cudaError_t launch_d2q9_diag(const S* f, const R* macro, const uint16_t* info, i
                              int pitch, long long plane, R rho0, double* partials, int nblocks,
                              cudaStream_t st);
 
+// Record the calling thread's last error (fixed buffer, no allocation).
+void set_thread_error(const char* msg);
+
 }  // namespace lbm
