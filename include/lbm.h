@@ -210,6 +210,27 @@ int lbm_num_tile_variants(void);
  * first use); 0 launches every step individually.  Results are identical. */
 lbm_status lbm_set_graph_mode(lbm_ctx* ctx, int use_graphs);
 
+/* FP64 mass of each component of caller-owned D2Q9 populations, for callers
+ * that cannot allocate device memory (a process whose device memory is all
+ * owned by another allocator or arena).  The paper has no counterpart: this
+ * is the lbm_get_diagnostics mass tally without a context and without any
+ * cudaMalloc.
+ *  f         device populations [2][9][ny][pitch], float (precision =
+ *            LBM_FP32) or double (LBM_FP64); read only.
+ *  solid     device mask [ny][pitch], non-zero = solid (skipped); may be NULL.
+ *  mass      device output, 2 doubles (sum over fluid nodes of sum_i f_i).
+ *  cuda_stream  stream to enqueue on (NULL = legacy default stream).
+ * The per-row partial sums live in one fixed device array of 65536 rows x 2
+ * doubles (1 MiB) that every GPU loading this library keeps until process
+ * exit; ny > 65536 is rejected with LBM_ERR_INVALID_ARG.  Every call on a
+ * device reuses that array, so calls that overlap on the GPU (concurrent
+ * streams or host threads) race and give wrong sums; serialise them.  The
+ * first call on each device (with that device current) resolves the
+ * array's device address: make that first call before any stream capture.
+ * Returns without waiting; the result is ready when the stream reaches it. */
+lbm_status lbm_mass_noalloc(const void* f, int precision, int nx, int ny, int pitch,
+                            const uint8_t* solid, double* mass, void* cuda_stream);
+
 /* Release all device memory of the context.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);
 

@@ -107,6 +107,9 @@ def load():
     L.lbm_num_tile_variants.argtypes = []
     L.lbm_set_graph_mode.restype = ctypes.c_int
     L.lbm_set_graph_mode.argtypes = [c_ctx, ctypes.c_int]
+    L.lbm_mass_noalloc.restype = ctypes.c_int
+    L.lbm_mass_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.lbm_version.restype = ctypes.c_char_p
     L.lbm_version.argtypes = []
     _lib = L
@@ -251,6 +254,15 @@ class Solver:
 
     def load_checkpoint(self, path):
         _check(load().lbm_load(self.h, path.encode()), self.h)
+
+
+def mass_noalloc(f_ptr, precision, nx, ny, pitch, solid_ptr, mass_ptr, stream=None):
+    """FP64 component masses of caller-owned device populations, written to
+    the caller's device pair `mass_ptr`; allocates no device memory."""
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(load().lbm_mass_noalloc(ctypes.c_void_p(f_ptr), p, int(nx), int(ny), int(pitch),
+                                   ctypes.c_void_p(solid_ptr or 0), ctypes.c_void_p(mass_ptr),
+                                   ctypes.c_void_p(stream or 0)), None)
 
 
 def version():
