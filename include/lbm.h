@@ -199,9 +199,16 @@ lbm_status lbm_load(lbm_ctx* ctx, const char* path);
 lbm_status lbm_enable_kernel_timing(lbm_ctx* ctx, int every);
 lbm_status lbm_kernel_time(lbm_ctx* ctx, double* mean_ms, int64_t* samples);
 
+/* The same samples split by launch: the fast tile list (interior and edge
+ * tiles) and the general tile list (tiles that see an open face), each a
+ * mean device duration in milliseconds (0 for an empty list). */
+lbm_status lbm_kernel_time_split(lbm_ctx* ctx, double* fast_ms, double* general_ms, int64_t* samples);
+
 /* Tile shape of the fused step kernel: variant in [0, lbm_num_tile_variants()),
- * 0: 32x8, 1: 32x4, 2: 64x4, 3: 32x16 nodes per CTA (default 3).  Results do
- * not depend on the variant; only speed does. */
+ * 0: 32x8, 1: 32x4, 2: 64x4, 3: 32x16 nodes per CTA (default: 1 below 2^22
+ * nodes, else 0).  Bit-identical results on grids without open faces; with
+ * open faces the FP64 flux partials are grouped per tile, so chi may differ
+ * in its last bit. */
 lbm_status lbm_set_tile_variant(lbm_ctx* ctx, int variant);
 int lbm_num_tile_variants(void);
 

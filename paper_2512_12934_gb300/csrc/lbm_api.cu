@@ -58,14 +58,14 @@ struct lbm_ctx {
     uint16_t* info = nullptr;
     int* blocks = nullptr;          // tile list: fast tiles first, then general tiles
     uint8_t* block_flags = nullptr;
+    unsigned* block_strips = nullptr;
     int nfast = 0, ngeneral = 0;
     void* uin = nullptr;
     void* Fp[2] = {nullptr, nullptr};
     void* fo[2] = {nullptr, nullptr};
     double* scal[2] = {nullptr, nullptr};
-    double* partials = nullptr;
+    double* partials[2] = {nullptr, nullptr};  // FP64 flux partials per tile slot, ping-pong
     int* block_slot = nullptr;
-    unsigned int* counter = nullptr;
     unsigned int* status = nullptr;
     void* macro = nullptr;
     double* diag_partials = nullptr;
@@ -95,7 +95,7 @@ struct lbm_ctx {
     void* stage = nullptr;             // pinned staging buffer for host transfers
     size_t stage_bytes = 0;
     int timing_every = 0;
-    std::vector<cudaEvent_t> ev_start, ev_stop;
+    std::vector<cudaEvent_t> ev_start, ev_mid, ev_stop;
     int n_samples = 0;
     std::string err;
 };
@@ -130,9 +130,10 @@ void free_ctx(lbm_ctx* c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (cudaEvent_t e : c->ev_start) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_mid) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
-    void* ptrs[] = {c->f[0], c->f[1], c->info, c->blocks, c->block_flags, c->uin, c->Fp[0], c->Fp[1], c->fo[0], c->fo[1],
-                    c->scal[0], c->scal[1], c->partials, c->block_slot, c->counter, c->status,
+    void* ptrs[] = {c->f[0], c->f[1], c->info, c->blocks, c->block_flags, c->block_strips, c->uin, c->Fp[0], c->Fp[1], c->fo[0], c->fo[1],
+                    c->scal[0], c->scal[1], c->partials[0], c->partials[1], c->block_slot, c->status,
                     c->macro, c->diag_partials};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -159,6 +160,7 @@ D2Args<S, R> make_args(lbm_ctx* c, bool write_macros) {
     a.blocks = c->blocks;
     a.block_flags = c->block_flags;
     a.block_slot = c->block_slot;
+    a.block_strips = c->block_strips;
     a.list_off = 0;
     a.nfaces = c->nfaces;
     for (int i = 0; i < c->nfaces; ++i) a.face[i] = c->faces[i];
@@ -171,8 +173,8 @@ D2Args<S, R> make_args(lbm_ctx* c, bool write_macros) {
     a.fo_out = static_cast<R*>(c->fo[out]);
     a.scal_in = c->scal[in];
     a.scal_out = c->scal[out];
-    a.partials = c->partials;
-    a.counter = c->counter;
+    a.part_in = c->partials[in];
+    a.part_out = c->partials[out];
     a.nslots = c->nslots;
     a.macro = write_macros ? static_cast<R*>(c->macro) : nullptr;
     a.status = c->status;
@@ -190,7 +192,8 @@ D2Args<S, R> make_args(lbm_ctx* c, bool write_macros) {
 // Both tile lists of one step.  side != nullptr: the general list runs on a
 // forked branch (used while capturing graphs).
 template <typename S, typename R>
-cudaError_t launch_lists(lbm_ctx* c, bool macros, cudaStream_t st, cudaStream_t side) {
+cudaError_t launch_lists(lbm_ctx* c, bool macros, cudaStream_t st, cudaStream_t side,
+                         cudaEvent_t mid = nullptr) {
     D2Args<S, R> a = make_args<S, R>(c, macros);
     cudaError_t e = cudaSuccess;
     const bool fork = side && c->nfast > 0 && c->ngeneral > 0;
@@ -199,6 +202,7 @@ cudaError_t launch_lists(lbm_ctx* c, bool macros, cudaStream_t st, cudaStream_t 
         if (e == cudaSuccess) e = cudaStreamWaitEvent(side, c->ev_fork, 0);
     }
     if (e == cudaSuccess) e = launch_d2q9_step<S, R>(a, c->variant, false, c->nfast, st);
+    if (e == cudaSuccess && mid) e = cudaEventRecord(mid, st);
     a.list_off = c->nfast;
     if (e == cudaSuccess) e = launch_d2q9_step<S, R>(a, c->variant, true, c->ngeneral, fork ? side : st);
     if (fork && e == cudaSuccess) {
@@ -209,8 +213,8 @@ cudaError_t launch_lists(lbm_ctx* c, bool macros, cudaStream_t st, cudaStream_t 
 }
 
 template <typename S, typename R>
-lbm_status launch_one(lbm_ctx* c, bool macros, cudaStream_t st) {
-    cudaError_t e = launch_lists<S, R>(c, macros, st, nullptr);
+lbm_status launch_one(lbm_ctx* c, bool macros, cudaStream_t st, cudaEvent_t mid = nullptr) {
+    cudaError_t e = launch_lists<S, R>(c, macros, st, nullptr, mid);
     if (e != cudaSuccess) return cuda_fail(c, e, "d2q9 step launch");
     // the ping-pong slot written by this step becomes current
     c->cur = 1 - c->cur;
@@ -274,14 +278,16 @@ template <typename S, typename R>
 lbm_status launch_sampled(lbm_ctx* c, bool macros) {
     const int i = c->n_samples;
     if ((int)c->ev_start.size() <= i) {
-        cudaEvent_t a, b;
+        cudaEvent_t a, m, b;
         CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&m));
         CK(cudaEventCreate(&b));
         c->ev_start.push_back(a);
+        c->ev_mid.push_back(m);
         c->ev_stop.push_back(b);
     }
     CK(cudaEventRecord(c->ev_start[i], c->stream));
-    lbm_status st = launch_one<S, R>(c, macros, c->stream);
+    lbm_status st = launch_one<S, R>(c, macros, c->stream, c->ev_mid[i]);
     if (st != LBM_OK) return st;
     CK(cudaEventRecord(c->ev_stop[i], c->stream));
     c->n_samples += 1;
@@ -465,7 +471,7 @@ lbm_status init_state(lbm_ctx* c, const double* rho_init, const double* u_init, 
     CK(cudaMemset(c->Fp[0], 0, nfn * 8 * sizeof(R)));
     CK(cudaMemset(c->Fp[1], 0, nfn * 8 * sizeof(R)));
     CK(cudaMemset(c->status, 0, sizeof(unsigned int)));
-    CK(cudaMemset(c->counter, 0, sizeof(unsigned int)));
+    // lambda0 = 0, chi0 = 1; [5] = 0: no flux partials yet
     double sc[8] = {0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     CK(cudaMemcpy(c->scal[0], sc, sizeof(sc), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->scal[1], sc, sizeof(sc), cudaMemcpyHostToDevice));
@@ -506,6 +512,7 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
     // nodes or outlet-neighbour nodes join the flux reduction.
     std::vector<int> list_fast, list_gen;
     std::vector<uint8_t> fl_fast, fl_gen;
+    std::vector<unsigned> strips_gen;
     std::vector<int> slots;
     for (unsigned by = 0; by < c->gdim.y; ++by)
         for (unsigned bx = 0; bx < c->gdim.x; ++bx) {
@@ -532,8 +539,43 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
             if (near_solid || closed_edge || gen) fl |= BLOCK_SOLID;
             const int packed = (int)bx | ((int)by << 16);
             if (gen) {
+                // face sides seen by the tile's psi halo (after the ghost mirror):
+                // each gets a strip of face nodes reconstructed once per tile
+                int cnt[4] = {0, 0, 0, 0};
+                bool sees_outlet = false;
+                for (int yy = y0 - 2; yy < y0 + c->ty + 2; ++yy)
+                    for (int xx = x0 - 2; xx < x0 + c->tx + 2; ++xx) {
+                        int gx = xx, gy = yy;
+                        if (gx < 0 || gx >= nx) {
+                            if (grid->periodic[0]) gx = ((gx % nx) + nx) % nx;
+                            else if (c->open_side[gx < 0 ? 0 : 1]) gx = gx < 0 ? -1 - gx : 2 * nx - 1 - gx;
+                            else continue;
+                        }
+                        if (gy < 0 || gy >= ny) {
+                            if (grid->periodic[1]) gy = ((gy % ny) + ny) % ny;
+                            else if (c->open_side[gy < 0 ? 2 : 3]) gy = gy < 0 ? -1 - gy : 2 * ny - 1 - gy;
+                            else continue;
+                        }
+                        if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;
+                        const int fid = faceid[(size_t)gy * nx + gx];
+                        if (fid) {
+                            cnt[c->faces[fid - 1].side] += 1;
+                            if (c->faces[fid - 1].kind == FACE_OUTLET) sees_outlet = true;
+                        }
+                    }
+                unsigned strips = 0;
+                int nstrip = 0;
+                for (int pass = 0; pass < 2; ++pass) {
+                    int best = -1;
+                    for (int sd = 0; sd < 4; ++sd)
+                        if (cnt[sd] > 0 && (best < 0 || cnt[sd] > cnt[best])) best = sd;
+                    if (best < 0) break;
+                    strips |= (unsigned)(best + 1) << (8 * nstrip++);
+                    cnt[best] = 0;
+                }
+                strips_gen.push_back(strips);
                 list_gen.push_back(packed);
-                fl_gen.push_back(fl | BLOCK_GENERAL);
+                fl_gen.push_back(fl | BLOCK_GENERAL | (sees_outlet ? BLOCK_LAMBDA : 0u));
                 slots.push_back(part ? c->nslots++ : -1);
             } else {
                 list_fast.push_back(packed);
@@ -548,14 +590,17 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
     bflags.insert(bflags.end(), fl_gen.begin(), fl_gen.end());
     std::vector<int> slot_all((size_t)c->nfast, -1);
     slot_all.insert(slot_all.end(), slots.begin(), slots.end());
+    std::vector<unsigned> strip_all((size_t)c->nfast, 0u);
+    strip_all.insert(strip_all.end(), strips_gen.begin(), strips_gen.end());
 
-    void* old[] = {c->blocks, c->block_flags, c->block_slot, c->partials};
+    void* old[] = {c->blocks, c->block_flags, c->block_slot, c->block_strips, c->partials[0], c->partials[1]};
     for (void* p : old)
         if (p) cudaFree(p);
     c->blocks = nullptr;
     c->block_flags = nullptr;
     c->block_slot = nullptr;
-    c->partials = nullptr;
+    c->block_strips = nullptr;
+    c->partials[0] = c->partials[1] = nullptr;
     for (int p = 0; p < 2; ++p)
         if (c->gexec[p]) {
             cudaGraphExecDestroy(c->gexec[p]);
@@ -564,11 +609,18 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
     CK(cudaMalloc((void**)&c->blocks, blist.size() * sizeof(int) + 4));
     CK(cudaMalloc((void**)&c->block_flags, bflags.size() + 4));
     CK(cudaMalloc((void**)&c->block_slot, slot_all.size() * sizeof(int) + 4));
-    CK(cudaMalloc((void**)&c->partials, (size_t)std::max(1, c->nslots) * 4 * 8));
+    CK(cudaMalloc((void**)&c->block_strips, strip_all.size() * sizeof(unsigned) + 4));
+    for (int p = 0; p < 2; ++p) {
+        CK(cudaMalloc((void**)&c->partials[p], (size_t)std::max(1, c->nslots) * 4 * 8));
+        CK(cudaMemset(c->partials[p], 0, (size_t)std::max(1, c->nslots) * 4 * 8));
+    }
+    CK(cudaMemcpy(c->block_strips, strip_all.data(), strip_all.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->blocks, blist.data(), blist.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->block_flags, bflags.data(), bflags.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->block_slot, slot_all.data(), slot_all.size() * sizeof(int), cudaMemcpyHostToDevice));
-    CK(cudaMemset(c->counter, 0, sizeof(unsigned int)));
+    // a new tiling renumbers the slots: the partials of the old tiling are void
+    CK(cudaMemset(c->scal[0] + 5, 0, sizeof(double)));
+    CK(cudaMemset(c->scal[1] + 5, 0, sizeof(double)));
     return LBM_OK;
 }
 
@@ -757,11 +809,11 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
     c->diag_blocks = 152 * 4;
     cudaError_t e = cudaGetDevice(&c->device);
     void** allocs[] = {&c->f[0], &c->f[1], (void**)&c->info, &c->uin, &c->Fp[0], &c->Fp[1], &c->fo[0], &c->fo[1],
-                       (void**)&c->scal[0], (void**)&c->scal[1], (void**)&c->counter, (void**)&c->status, &c->macro, (void**)&c->diag_partials};
+                       (void**)&c->scal[0], (void**)&c->scal[1], (void**)&c->status, &c->macro, (void**)&c->diag_partials};
     const size_t sizes[] = {fbytes, fbytes, (size_t)c->plane * 2, (size_t)nfn * c->rbytes,
                             (size_t)nfn * 8 * c->rbytes, (size_t)nfn * 8 * c->rbytes,
                             (size_t)nfn * 18 * c->rbytes, (size_t)nfn * 18 * c->rbytes, 64, 64,
-                            16, 16,
+                            16,
                             (size_t)4 * c->plane * c->rbytes, (size_t)c->diag_blocks * 3 * 8};
     for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]) && e == cudaSuccess; ++i) {
         e = cudaMalloc(allocs[i], sizes[i]);
@@ -802,7 +854,10 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
     c->host_solid_in.assign(sol.begin(), sol.end());
     c->h_faceid = faceid;
     c->h_nbrid = nbrid;
-    lbm_status st = build_tiles(c, 3, false);
+    // default tile shape: narrow tiles (more CTAs, shorter chains) for small
+    // grids, 32x8 for large ones (measured on GB300; lbm_set_tile_variant
+    // overrides)
+    lbm_status st = build_tiles(c, (long long)nx * ny < (1LL << 22) ? 1 : 0, false);
     if (st != LBM_OK) {
         const std::string msg = c->err;
         free_ctx(c);
@@ -902,10 +957,25 @@ lbm_status lbm_get_diagnostics(lbm_ctx* c, lbm_diag* out) {
     }
     out->mass[0] = m0;
     out->mass[1] = m1;
+    // lambda / chi the next step will use: the same sums the outlet tiles form
     out->lambda = sc[0];
     out->chi = sc[1];
-    out->q_in = sc[2];
-    out->q_out = sc[3];
+    out->q_in = 0.0;
+    out->q_out = 0.0;
+    if (sc[5] != 0.0 && c->nslots > 0) {
+        std::vector<double> pp((size_t)c->nslots * 4);
+        CK(cudaMemcpy(pp.data(), c->partials[c->cur], pp.size() * 8, cudaMemcpyDeviceToHost));
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int sl = 0; sl < c->nslots; ++sl)
+            for (int j = 0; j < 4; ++j) t[j] += pp[(size_t)sl * 4 + j];
+        out->q_in = t[0];
+        out->q_out = t[1];
+        if (c->out_face >= 0 && t[3] > 0.0) {
+            const double um = t[2] / t[3];
+            out->lambda = um > 0.0 ? um : 0.0;
+            out->chi = (!c->have_inlet || std::fabs(t[1]) < 1e-14) ? 1.0 : t[0] / t[1];
+        }
+    }
     out->max_speed = std::sqrt(u2);
     out->step = c->step;
     out->launches = c->launches;
@@ -921,7 +991,8 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
     const size_t fbytes = (size_t)18 * c->plane * c->sbytes;
     const size_t nfn = (size_t)std::max(1, c->nface_nodes);
     const size_t mbytes = (size_t)4 * c->plane * c->rbytes;
-    std::vector<char> buf(fbytes + nfn * 8 * c->rbytes + nfn * 18 * c->rbytes + 64 + mbytes);
+    const size_t pbytes = (size_t)std::max(1, c->nslots) * 4 * 8;
+    std::vector<char> buf(fbytes + nfn * 8 * c->rbytes + nfn * 18 * c->rbytes + 64 + mbytes + pbytes);
     char* p = buf.data();
     CK(cudaMemcpy(p, c->f[c->cur], fbytes, cudaMemcpyDeviceToHost));
     p += fbytes;
@@ -932,7 +1003,9 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
     CK(cudaMemcpy(p, c->scal[c->cur], 64, cudaMemcpyDeviceToHost));
     p += 64;
     CK(cudaMemcpy(p, c->macro, mbytes, cudaMemcpyDeviceToHost));
-    const char magic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+    p += mbytes;
+    CK(cudaMemcpy(p, c->partials[c->cur], pbytes, cudaMemcpyDeviceToHost));
+    const char magic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '2'};
     const int64_t hdr[6] = {c->nx, c->ny, c->precision, c->nface_nodes, c->step, (int64_t)buf.size()};
     bool ok = std::fwrite(magic, 1, 8, fp) == 8 && std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 &&
               std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
@@ -950,8 +1023,9 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
     const size_t fbytes = (size_t)18 * c->plane * c->sbytes;
     const size_t nfn = (size_t)std::max(1, c->nface_nodes);
     const size_t mbytes = (size_t)4 * c->plane * c->rbytes;
-    const size_t total = fbytes + nfn * 8 * c->rbytes + nfn * 18 * c->rbytes + 64 + mbytes;
-    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "LBMCKPT1", 8) == 0 &&
+    const size_t pbytes = (size_t)std::max(1, c->nslots) * 4 * 8;
+    const size_t total = fbytes + nfn * 8 * c->rbytes + nfn * 18 * c->rbytes + 64 + mbytes + pbytes;
+    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "LBMCKPT2", 8) == 0 &&
               std::fread(hdr, sizeof(hdr), 1, fp) == 1 && hdr[0] == c->nx && hdr[1] == c->ny &&
               hdr[2] == c->precision && hdr[3] == c->nface_nodes && hdr[5] == (int64_t)total;
     std::vector<char> buf(total);
@@ -969,6 +1043,8 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
     CK(cudaMemcpy(c->scal[c->cur], p, 64, cudaMemcpyHostToDevice));
     p += 64;
     CK(cudaMemcpy(c->macro, p, mbytes, cudaMemcpyHostToDevice));
+    p += mbytes;
+    CK(cudaMemcpy(c->partials[c->cur], p, pbytes, cudaMemcpyHostToDevice));
     c->step = hdr[4];
     return LBM_OK;
 }
@@ -982,16 +1058,27 @@ lbm_status lbm_enable_kernel_timing(lbm_ctx* c, int every) {
 }
 
 lbm_status lbm_kernel_time(lbm_ctx* c, double* mean_ms, int64_t* samples) {
-    if (!c || !mean_ms || !samples) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    double fast = 0.0, gen = 0.0;
+    lbm_status st = lbm_kernel_time_split(c, &fast, &gen, samples);
+    if (st != LBM_OK) return st;
+    *mean_ms = fast + gen;
+    return LBM_OK;
+}
+
+lbm_status lbm_kernel_time_split(lbm_ctx* c, double* fast_ms, double* general_ms, int64_t* samples) {
+    if (!c || !fast_ms || !general_ms || !samples) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
     CK(cudaStreamSynchronize(c->stream));
-    double tot = 0.0;
+    double tf = 0.0, tg = 0.0;
     for (int i = 0; i < c->n_samples; ++i) {
-        float ms = 0.0f;
-        CK(cudaEventElapsedTime(&ms, c->ev_start[i], c->ev_stop[i]));
-        tot += ms;
+        float a = 0.0f, b = 0.0f;
+        CK(cudaEventElapsedTime(&a, c->ev_start[i], c->ev_mid[i]));
+        CK(cudaEventElapsedTime(&b, c->ev_mid[i], c->ev_stop[i]));
+        tf += a;
+        tg += b;
     }
     *samples = c->n_samples;
-    *mean_ms = c->n_samples ? tot / c->n_samples : 0.0;
+    *fast_ms = c->n_samples ? tf / c->n_samples : 0.0;
+    *general_ms = c->n_samples ? tg / c->n_samples : 0.0;
     return LBM_OK;
 }
 

@@ -15,6 +15,8 @@
 //   reductions that set lambda and chi for the next step (Eqs. 21, 23).
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -130,13 +132,22 @@ __device__ __forceinline__ R jy_of(const R (&g)[9]) {
     return (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
 }
 
-// Open-face reconstruction of the unknown populations of a face node:
-// inlet Eq. 13/14 + alpha (Eqs. 15-19), outlet Eq. 20 with lambda.
-template <typename S, typename R>
-__device__ __forceinline__ void face_fix(const D2Args<S, R>& a, int x, int y, int fid, R (&f)[2][9]) {
-    const FaceDev& F = a.face[fid];
-    const int slot = F.base + ((F.side <= 1) ? y : x) - F.lo;
-    const int x2 = x - F.ox, y2 = y - F.oy;  // inward neighbour
+// Outward normal of a grid side (0: x=0, 1: x=nx-1, 2: y=0, 3: y=ny-1).
+__host__ __device__ constexpr int side_ox(int side) { return side == 0 ? -1 : (side == 1 ? 1 : 0); }
+__host__ __device__ constexpr int side_oy(int side) { return side == 2 ? -1 : (side == 3 ? 1 : 0); }
+// Direction i is unknown at a node of that side when it points into the domain.
+__host__ __device__ constexpr bool unknown_(int side, int i) {
+    return ex_(i) * side_ox(side) + ey_(i) * side_oy(side) < 0;
+}
+
+// Open-face reconstruction of the unknown populations of a face node on side
+// SIDE: inlet Eq. 13/14 + alpha (Eqs. 15-19), outlet Eq. 20 with lambda.
+template <int SIDE, typename S, typename R>
+__device__ __forceinline__ void face_fix_side(const D2Args<S, R>& a, const FaceDev& F, int x, int y, R lam,
+                                              R (&f)[2][9]) {
+    constexpr int OX = side_ox(SIDE), OY = side_oy(SIDE);
+    const int slot = F.base + ((SIDE <= 1) ? y : x) - F.lo;
+    const int x2 = x - OX, y2 = y - OY;  // inward neighbour
     const unsigned info2 = a.info[y2 * a.pitch + x2];
     R g[2][9];
     pull_wrap(a, x2, y2, info2, g);
@@ -148,42 +159,55 @@ __device__ __forceinline__ void face_fix(const D2Args<S, R>& a, int x, int y, in
         const R inv2 = R(1) / (r20 + r21);
         const R u2x = jx * inv2, u2y = jy * inv2;
         const R sp = a.uin[slot];
-        const R uix = -R(F.ox) * sp, uiy = -R(F.oy) * sp;
+        const R uix = R(-OX) * sp, uiy = R(-OY) * sp;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const R rin = R(F.rho_in[k]);
             const R r2 = k == 0 ? r20 : r21;
 #pragma unroll
             for (int i = 0; i < 9; ++i)
-                if (ex_(i) * F.ox + ey_(i) * F.oy < 0)  // unknown: points into the domain
+                if (unknown_(SIDE, i))
                     f[k][i] = feq_<R>(i, rin, uix, uiy) + (g[k][i] - feq_<R>(i, r2, u2x, u2y));
             if (F.alpha) {
                 const R mx = jx_of(f[k]) + R(0.5) * Fp[k * 2 + 0];
                 const R my = jy_of(f[k]) + R(0.5) * Fp[k * 2 + 1];
-                const R cx = (rin * uix - mx) / R(F.sxx), cy = (rin * uiy - my) / R(F.syy);
+                // sum over the unknown set of w e_x^2 and w e_y^2 (1/6 normal, 1/18 tangential)
+                constexpr R SXX = OX != 0 ? R(1) / R(6) : R(1) / R(18);
+                constexpr R SYY = OY != 0 ? R(1) / R(6) : R(1) / R(18);
+                const R cx = (rin * uix - mx) / SXX, cy = (rin * uiy - my) / SYY;
 #pragma unroll
                 for (int i = 0; i < 9; ++i)
-                    if (ex_(i) * F.ox + ey_(i) * F.oy < 0)
-                        f[k][i] += w_<R>(i) * (R(ex_(i)) * cx + R(ey_(i)) * cy);
+                    if (unknown_(SIDE, i)) f[k][i] += w_<R>(i) * (R(ex_(i)) * cx + R(ey_(i)) * cy);
             }
         }
     } else {
-        const R lam = R(a.scal_in[0]);
         const R inv = R(1) / (R(1) + lam);
         const R* fo = a.fo_in + slot * 18;
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            if (ex_(i) * F.ox + ey_(i) * F.oy < 0)
+            if (unknown_(SIDE, i))
 #pragma unroll
                 for (int k = 0; k < 2; ++k) f[k][i] = (fo[i * 2 + k] + lam * g[k][i]) * inv;
     }
 }
 
 template <typename S, typename R>
-__device__ __forceinline__ void pull_general(const D2Args<S, R>& a, int x, int y, unsigned info, R (&f)[2][9]) {
+__device__ __forceinline__ void face_fix(const D2Args<S, R>& a, int x, int y, int fid, R lam, R (&f)[2][9]) {
+    const FaceDev& F = a.face[fid];
+    switch (F.side) {
+    case 0: face_fix_side<0>(a, F, x, y, lam, f); break;
+    case 1: face_fix_side<1>(a, F, x, y, lam, f); break;
+    case 2: face_fix_side<2>(a, F, x, y, lam, f); break;
+    default: face_fix_side<3>(a, F, x, y, lam, f); break;
+    }
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void pull_general(const D2Args<S, R>& a, int x, int y, unsigned info, R lam,
+                                             R (&f)[2][9]) {
     pull_wrap(a, x, y, info, f);
     const int fid = (int)((info >> INFO_FACE_SHIFT) & 7u);
-    if (fid) face_fix(a, x, y, fid - 1, f);
+    if (fid) face_fix(a, x, y, fid - 1, lam, f);
 }
 
 // Virtual site of the psi stencil: periodic wrap, ghost mirror across an open
@@ -233,13 +257,13 @@ __device__ __forceinline__ bool resolve_closed(const D2Args<S, R>& a, int& gx, i
 // Tile modes: 0 deep interior, 1 edge (wrap / closed edges), 2 general.
 // Density pair of a halo site (no populations kept).  Returns false if solid.
 template <typename S, typename R, int MODE>
-__device__ __forceinline__ bool site_rho(const D2Args<S, R>& a, int gx, int gy, R& r0, R& r1) {
+__device__ __forceinline__ bool site_rho(const D2Args<S, R>& a, int gx, int gy, R& r0, R& r1, R lam = R(0)) {
     if (MODE == 2) {
         if (resolve_site(a, gx, gy)) return false;
         const unsigned inf = a.info[gy * a.pitch + gx];
         if (inf & INFO_SOLID) return false;
         R g[2][9];
-        pull_general(a, gx, gy, inf, g);
+        pull_general(a, gx, gy, inf, lam, g);
         r0 = rho_of(g[0]);
         r1 = rho_of(g[1]);
     } else if (MODE == 1) {
@@ -268,6 +292,17 @@ struct TileSmem {
     unsigned char sol[TY + 4][TX + 4];
     R un[TX > TY ? TX : TY];
     double red[TX * TY / 32][4];
+    R lam, chi;  // outlet coefficients of this step (general tiles that see the outlet)
+};
+
+// General tiles also keep up to two face strips: the face nodes of one grid
+// side along the tile's halo range, each reconstructed once per tile.
+template <typename S, typename R, int TX, int TY>
+struct TileSmemGen : TileSmem<S, R, TX, TY> {
+    static constexpr int SL = (TX > TY ? TX : TY) + 4;  // strip entries (halo range)
+    static constexpr int SO = (TX > TY ? TX : TY);      // own entries
+    R fs_rho[2][SL][2];
+    R fs_f[2][SO][18];
 };
 
 // Stage the tile's densities (own node + two-node halo) in shared memory;
@@ -287,7 +322,7 @@ __device__ __forceinline__ void stage_tile(const D2Args<S, R>& a, TileSmem<S, R,
             info = a.info[y * a.pitch + x];
             fluid = !(info & INFO_SOLID);
             if (fluid) {
-                if (MODE == 2) pull_general(a, x, y, info, f);
+                if (MODE == 2) pull_general(a, x, y, info, R(0), f);
                 else pull_wrap(a, x, y, info, f);
                 r0 = rho_of(f[0]);
                 r1 = rho_of(f[1]);
@@ -312,7 +347,7 @@ __device__ __forceinline__ void stage_tile(const D2Args<S, R>& a, TileSmem<S, R,
     sm.sol[ty + 2][tx + 2] = sol;
     // halo ring: densities only
     constexpr int RING = RX * RY - TX * TY;
-    for (int p = threadIdx.x; p < RING; p += NT) {
+    auto ring_site = [&](int p) {
         int rx, ry;
         if (p < 2 * RX) {                // two rows above
             ry = p / RX;
@@ -331,13 +366,209 @@ __device__ __forceinline__ void stage_tile(const D2Args<S, R>& a, TileSmem<S, R,
         sm.rho[0][ry][rx] = h0;
         sm.rho[1][ry][rx] = h1;
         sm.sol[ry][rx] = ok ? 0 : 1;
+    };
+    if (RING <= NT) {
+        if ((int)threadIdx.x < RING) ring_site(threadIdx.x);
+    } else {
+        for (int p = threadIdx.x; p < RING; p += NT) ring_site(p);
+    }
+}
+
+// Strip geometry: entry e of a strip on side `side` is node (sx, sy).
+template <int TX, int TY>
+__device__ __forceinline__ void strip_node(int side, int e, int x0, int y0, int nx, int ny, int& sx, int& sy) {
+    if (side <= 1) {
+        sx = side == 0 ? 0 : nx - 1;
+        sy = y0 - 2 + e;
+    } else {
+        sx = x0 - 2 + e;
+        sy = side == 2 ? 0 : ny - 1;
+    }
+}
+
+// Strip slot of an in-grid site on a face side of this tile, or -1.
+template <int TX, int TY>
+__device__ __forceinline__ int strip_entry(int side, int gx, int gy, int x0, int y0, int nx, int ny) {
+    const int SL = side <= 1 ? TY + 4 : TX + 4;
+    int e = -1;
+    if (side == 0 && gx == 0) e = gy - (y0 - 2);
+    else if (side == 1 && gx == nx - 1) e = gy - (y0 - 2);
+    else if (side == 2 && gy == 0) e = gx - (x0 - 2);
+    else if (side == 3 && gy == ny - 1) e = gx - (x0 - 2);
+    return (e >= 0 && e < SL) ? e : -1;
+}
+
+// General-tile staging.  Threads without halo-ring work reconstruct the face
+// nodes of the tile's strips (inlet Eqs. 13-19 / outlet Eq. 20) once each;
+// own nodes and halo sites that are such face nodes read the result from
+// shared memory instead of repeating the reconstruction.
+template <typename S, typename R, int TX, int TY>
+__device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSmemGen<S, R, TX, TY>& sm, int x0,
+                                                   int y0, int tx, int ty, unsigned strips, unsigned bflags,
+                                                   R (&f)[2][9], unsigned& info, bool& fluid) {
+    constexpr int RX = TX + 4, RY = TY + 4, NT = TX * TY;
+    constexpr int RING = RX * RY - TX * TY;
+    const int tid = threadIdx.x;
+    // ---- lambda (Eq. 21) and chi (Eq. 23) from the previous step's FP64 flux
+    // partials: one warp, fixed order (the same in every tile that needs them)
+    if (bflags & BLOCK_LAMBDA) {
+        if (tid >= NT - 32) {
+            const int lane = tid & 31;
+            const bool valid = a.scal_in[5] != 0.0;
+            double t[4] = {0.0, 0.0, 0.0, 0.0};
+            if (valid)
+                for (int sl = lane; sl < a.nslots; sl += 32)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) t[j] += a.part_in[sl * 4 + j];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t[j] += __shfl_down_sync(0xffffffffu, t[j], o);
+            if (lane == 0) {
+                double lam = a.scal_in[0], chi = a.scal_in[1];
+                if (valid && a.out_face >= 0 && t[3] > 0.0) {
+                    const double um = t[2] / t[3];
+                    lam = um > 0.0 ? um : 0.0;
+                    chi = (!a.have_inlet || fabs(t[1]) < 1e-14) ? 1.0 : t[0] / t[1];
+                }
+                sm.lam = R(lam);
+                sm.chi = R(chi);
+            }
+        }
+        __syncthreads();
+    }
+    const R lam = (bflags & BLOCK_LAMBDA) ? sm.lam : R(0);
+    const int side0 = (int)(strips & 0xffu) - 1, side1 = (int)((strips >> 8) & 0xffu) - 1;
+    const int len0 = side0 < 0 ? 0 : (side0 <= 1 ? RY : RX);
+    const int len1 = side1 < 0 ? 0 : (side1 <= 1 ? RY : RX);
+    auto strip_of = [&](int side) { return side == side0 ? 0 : (side == side1 ? 1 : -1); };
+
+    // ---- phase 0: face strips ----
+    {
+        const int base = RING <= NT ? RING : 0;
+        for (int t = tid - base; t >= 0 && t < len0 + len1; t += NT) {
+            const int j = t < len0 ? 0 : 1;
+            const int e = j == 0 ? t : t - len0;
+            const int side = j == 0 ? side0 : side1;
+            int sx, sy;
+            strip_node<TX, TY>(side, e, x0, y0, a.nx, a.ny, sx, sy);
+            if (sx < 0 || sx >= a.nx || sy < 0 || sy >= a.ny) continue;
+            const unsigned inf = a.info[sy * a.pitch + sx];
+            if ((inf & INFO_SOLID) || !((inf >> INFO_FACE_SHIFT) & 7u)) continue;
+            R g[2][9];
+            pull_general(a, sx, sy, inf, lam, g);
+            sm.fs_rho[j][e][0] = rho_of(g[0]);
+            sm.fs_rho[j][e][1] = rho_of(g[1]);
+            const int o = side <= 1 ? sy - y0 : sx - x0;
+            const bool own = sx >= x0 && sx < x0 + TX && sy >= y0 && sy < y0 + TY;
+            if (own)
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) sm.fs_f[j][o][k * 9 + i] = g[k][i];
+        }
+    }
+
+    // ---- own node ----
+    const int x = x0 + tx, y = y0 + ty;
+    const bool inb = (x >= 0 && x < a.nx && y >= 0 && y < a.ny);
+    info = INFO_SOLID;
+    fluid = false;
+    int own_strip = -1, own_idx = 0;
+    R r0 = R(0), r1 = R(0);
+    unsigned char sol = 1;
+    if (inb) {
+        info = a.info[y * a.pitch + x];
+        fluid = !(info & INFO_SOLID);
+        if (fluid) {
+            const int fid = (int)((info >> INFO_FACE_SHIFT) & 7u);
+            if (fid) {
+                const int side = a.face[fid - 1].side;
+                own_strip = strip_of(side);
+                own_idx = side <= 1 ? ty : tx;
+            }
+            if (own_strip < 0) {
+                pull_general(a, x, y, info, lam, f);
+                r0 = rho_of(f[0]);
+                r1 = rho_of(f[1]);
+            }
+            sol = 0;
+        }
+    } else if (site_rho<S, R, 2>(a, x, y, r0, r1, lam)) {
+        sol = 0;
+    }
+    sm.rho[0][ty + 2][tx + 2] = r0;
+    sm.rho[1][ty + 2][tx + 2] = r1;
+    sm.sol[ty + 2][tx + 2] = sol;
+
+    // ---- halo ring ----
+    int def_j = -1, def_e = 0, def_rx = 0, def_ry = 0;
+    for (int p = tid; p < RING; p += NT) {
+        int rx, ry;
+        if (p < 2 * RX) {
+            ry = p / RX;
+            rx = p % RX;
+        } else if (p < 4 * RX) {
+            ry = TY + 2 + (p - 2 * RX) / RX;
+            rx = (p - 2 * RX) % RX;
+        } else {
+            const int q = p - 4 * RX;
+            ry = 2 + q / 4;
+            const int c = q % 4;
+            rx = c < 2 ? c : TX + c;
+        }
+        int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+        R h0 = R(0), h1 = R(0);
+        unsigned char hs = 1;
+        if (!resolve_site(a, gx, gy)) {
+            const unsigned inf = a.info[gy * a.pitch + gx];
+            if (!(inf & INFO_SOLID)) {
+                hs = 0;
+                const int fid = (int)((inf >> INFO_FACE_SHIFT) & 7u);
+                int j = -1, e = -1;
+                if (fid) {
+                    const int side = a.face[fid - 1].side;
+                    j = strip_of(side);
+                    if (j >= 0) e = strip_entry<TX, TY>(side, gx, gy, x0, y0, a.nx, a.ny);
+                }
+                if (j >= 0 && e >= 0 && RING <= NT) {
+                    def_j = j;  // filled from the strip after the barrier
+                    def_e = e;
+                    def_rx = rx;
+                    def_ry = ry;
+                } else {
+                    R g[2][9];
+                    pull_general(a, gx, gy, inf, lam, g);
+                    h0 = rho_of(g[0]);
+                    h1 = rho_of(g[1]);
+                }
+            }
+        }
+        sm.rho[0][ry][rx] = h0;
+        sm.rho[1][ry][rx] = h1;
+        sm.sol[ry][rx] = hs;
+    }
+    __syncthreads();
+    if (own_strip >= 0) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[k][i] = sm.fs_f[own_strip][own_idx][k * 9 + i];
+        sm.rho[0][ty + 2][tx + 2] = rho_of(f[0]);
+        sm.rho[1][ty + 2][tx + 2] = rho_of(f[1]);
+    }
+    if (def_j >= 0) {
+        sm.rho[0][def_ry][def_rx] = sm.fs_rho[def_j][def_e][0];
+        sm.rho[1][def_ry][def_rx] = sm.fs_rho[def_j][def_e][1];
     }
 }
 
 template <typename S, typename R, int TX, int TY, bool GEN>
 __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
     constexpr int NT = TX * TY, NW = NT / 32;
-    __shared__ TileSmem<S, R, TX, TY> sm;
+    using SmemT = typename std::conditional<GEN, TileSmemGen<S, R, TX, TY>, TileSmem<S, R, TX, TY>>::type;
+    __shared__ SmemT smx;
+    TileSmem<S, R, TX, TY>& sm = smx;
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
@@ -350,7 +581,8 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
     R f[2][9];
     unsigned info;
     bool fluid;
-    if (GEN) stage_tile<S, R, TX, TY, 2>(a, sm, x0, y0, tx, ty, f, info, fluid);
+    if constexpr (GEN)
+        stage_tile_general<S, R, TX, TY>(a, smx, x0, y0, tx, ty, a.block_strips[li], bflags, f, info, fluid);
     else if (bflags & BLOCK_EDGE) stage_tile<S, R, TX, TY, 1>(a, sm, x0, y0, tx, ty, f, info, fluid);
     else stage_tile<S, R, TX, TY, 0>(a, sm, x0, y0, tx, ty, f, info, fluid);
     __syncthreads();
@@ -419,7 +651,7 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
             if (fluid && nbr_face == a.out_face) sm.un[along] = (OF.side <= 1) ? ux : uy;
             __syncthreads();
             if (fluid && own_face == a.out_face) {
-                const R chi = R(a.scal_in[1]);
+                const R chi = sm.chi;
                 if (OF.side <= 1) ux = chi * sm.un[along];
                 else uy = chi * sm.un[along];
             }
@@ -436,13 +668,13 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
                 R* Fp = a.Fp_out + slot * 8;
                 Fp[0] = Fx0; Fp[1] = Fy0; Fp[2] = Fx1; Fp[3] = Fy1;
             } else {
+                // outlet: keep all nine pairs (only the unknown set is read back)
                 R* fo = a.fo_out + slot * 18;
 #pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (ex_(i) * F.ox + ey_(i) * F.oy < 0) {
-                        fo[i * 2 + 0] = f[0][i];
-                        fo[i * 2 + 1] = f[1][i];
-                    }
+                for (int i = 0; i < 9; ++i) {
+                    fo[i * 2 + 0] = f[0][i];
+                    fo[i * 2 + 1] = f[1][i];
+                }
             }
         }
         if (nbr_face >= 0 && a.face[nbr_face].kind == FACE_INLET) {
@@ -539,31 +771,13 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
                 for (int j = 0; j < 4; ++j) sm.red[tid >> 5][j] = v[j];
             __syncthreads();
             if (tid == 0) {
+                // plain stores: the next step's outlet tiles read them after the
+                // kernel boundary, so no fence or atomic is needed
                 double acc[4] = {0.0, 0.0, 0.0, 0.0};
                 for (int wgrp = 0; wgrp < NW; ++wgrp)
                     for (int j = 0; j < 4; ++j) acc[j] += sm.red[wgrp][j];
-                for (int j = 0; j < 4; ++j) a.partials[slot * 4 + j] = acc[j];
-                __threadfence();
-                const unsigned done = atomicAdd(a.counter, 1u);
-                if (done == (unsigned)(a.nslots - 1)) {
-                    __threadfence();
-                    double tot[4] = {0.0, 0.0, 0.0, 0.0};
-                    const volatile double* pp = a.partials;
-                    for (int sl = 0; sl < a.nslots; ++sl)
-                        for (int j = 0; j < 4; ++j) tot[j] += pp[sl * 4 + j];
-                    double lam = a.scal_in[0], chi = a.scal_in[1], um = 0.0;
-                    if (a.out_face >= 0 && tot[3] > 0.0) {
-                        um = tot[2] / tot[3];
-                        lam = um > 0.0 ? um : 0.0;
-                        chi = (!a.have_inlet || fabs(tot[1]) < 1e-14) ? 1.0 : tot[0] / tot[1];
-                    }
-                    a.scal_out[0] = lam;
-                    a.scal_out[1] = chi;
-                    a.scal_out[2] = tot[0];
-                    a.scal_out[3] = tot[1];
-                    a.scal_out[4] = um;
-                    *a.counter = 0u;
-                }
+                for (int j = 0; j < 4; ++j) a.part_out[slot * 4 + j] = acc[j];
+                a.scal_out[5] = 1.0;
             }
         }
     }

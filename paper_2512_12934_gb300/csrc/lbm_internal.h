@@ -28,6 +28,7 @@ constexpr int MAX_FACES = 4;
 constexpr unsigned BLOCK_EDGE = 1u;     // pull or psi halo crosses a grid edge: wrap / closed-edge logic
 constexpr unsigned BLOCK_SOLID = 2u;    // a solid site lies within the tile's psi halo: adhesion
 constexpr unsigned BLOCK_GENERAL = 4u;  // general list
+constexpr unsigned BLOCK_LAMBDA = 8u;   // general tile that needs lambda / chi (sees outlet face nodes)
 
 constexpr int FACE_INLET = 1;
 constexpr int FACE_OUTLET = 2;
@@ -60,6 +61,7 @@ struct D2Args {
     const int* __restrict__ blocks;           // tile list: bx | by << 16
     const uint8_t* __restrict__ block_flags;  // per list entry: BLOCK_* flags
     const int* __restrict__ block_slot;       // per list entry: flux-reduction slot or -1
+    const unsigned* __restrict__ block_strips;  // per list entry: (side0 + 1) | (side1 + 1) << 8, 0 = none
     int list_off;                             // first list entry of this launch
     int nfaces;
     FaceDev face[MAX_FACES];
@@ -70,10 +72,10 @@ struct D2Args {
     R* __restrict__ Fp_out;
     const R* __restrict__ fo_in;    // [slot][9][2] outlet populations of the last step
     R* __restrict__ fo_out;
-    const double* __restrict__ scal_in;   // [0] lambda, [1] chi
-    double* __restrict__ scal_out;        // lambda, chi, Qin, Qout, Umean
-    double* partials;                     // [slot][4]
-    unsigned int* counter;
+    const double* __restrict__ scal_in;   // [0] initial lambda, [1] initial chi, [5] partials valid
+    double* __restrict__ scal_out;
+    const double* __restrict__ part_in;   // [slot][4] FP64 flux partials of the previous step
+    double* __restrict__ part_out;        // [slot][4] partials of this step: Qin, Qout, sum u_n, count
     int nslots;
     R* __restrict__ macro;                // optional [4][plane]: rho1, rho2, ux, uy
     unsigned int* status;

@@ -101,6 +101,9 @@ def load():
     L.lbm_enable_kernel_timing.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_kernel_time.restype = ctypes.c_int
     L.lbm_kernel_time.argtypes = [c_ctx, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.lbm_kernel_time_split.restype = ctypes.c_int
+    L.lbm_kernel_time_split.argtypes = [c_ctx, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64)]
     L.lbm_set_tile_variant.restype = ctypes.c_int
     L.lbm_set_tile_variant.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_num_tile_variants.restype = ctypes.c_int
@@ -242,6 +245,13 @@ class Solver:
         n = ctypes.c_int64()
         _check(load().lbm_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n)), self.h)
         return ms.value, n.value
+
+    def kernel_time_split(self):
+        a = ctypes.c_double()
+        b = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(load().lbm_kernel_time_split(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)), self.h)
+        return a.value, b.value, n.value
 
     def set_tile_variant(self, v):
         _check(load().lbm_set_tile_variant(self.h, int(v)), self.h)

@@ -180,7 +180,10 @@ def test_repeated_short_calls_equal_one_long_call():
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_tile_variants_and_graph_replay_agree(variant):
     """Tile shape and CUDA-graph replay change the schedule, not the result:
-    on a periodic grid (no reductions) every variant is bit-identical."""
+    on a periodic grid (no reductions) every variant is bit-identical.  With
+    open faces the FP64 flux partials are grouped per tile, so chi can differ
+    in its last bit between tile shapes; FP32 results then agree to the FP32
+    parity bar."""
     w = W.random_box(70, 45, 12, periodic=(1, 1), solid_frac=0.05, G12=0.9, Gw=(0.2, -0.1))
     a = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
     a.set_tile_variant(variant)
@@ -196,4 +199,4 @@ def test_tile_variants_and_graph_replay_agree(variant):
     q = lbm.Solver(c.cfg, c.solid, c.rho, c.u)
     q.set_graph_mode(0)
     q.step(70)
-    assert rel_inf(p.macros()[1], q.macros()[1]) < 1e-6
+    assert rel_inf(p.macros()[1], q.macros()[1]) < 1e-5
