@@ -212,6 +212,11 @@ lbm_status lbm_kernel_time_split(lbm_ctx* ctx, double* fast_ms, double* general_
 lbm_status lbm_set_tile_variant(lbm_ctx* ctx, int variant);
 int lbm_num_tile_variants(void);
 
+/* Current tiling: variant, number of tiles in the fast and general lists and
+ * the fluid nodes each list owns (every fluid node belongs to exactly one). */
+lbm_status lbm_tile_stats(lbm_ctx* ctx, int* variant, int* fast_tiles, int* general_tiles,
+                          int64_t* fast_nodes, int64_t* general_nodes);
+
 /* Step-replay mode: use_graphs != 0 (the default) replays runs of steps
  * from captured CUDA graphs (two launches per graph node pair, captured on
  * first use); 0 launches every step individually.  Results are identical. */

@@ -60,6 +60,7 @@ struct lbm_ctx {
     uint8_t* block_flags = nullptr;
     unsigned* block_strips = nullptr;
     int nfast = 0, ngeneral = 0;
+    int64_t fast_nodes = 0, general_nodes = 0;  // fluid nodes owned by each tile list
     void* uin = nullptr;
     void* Fp[2] = {nullptr, nullptr};
     void* fo[2] = {nullptr, nullptr};
@@ -513,6 +514,7 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
     std::vector<int> list_fast, list_gen;
     std::vector<uint8_t> fl_fast, fl_gen;
     std::vector<unsigned> strips_gen;
+    int64_t gen_nodes = 0, fast_nodes_cnt = 0;
     std::vector<int> slots;
     for (unsigned by = 0; by < c->gdim.y; ++by)
         for (unsigned bx = 0; bx < c->gdim.x; ++bx) {
@@ -538,6 +540,11 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
             if (edge) fl |= BLOCK_EDGE;
             if (near_solid || closed_edge || gen) fl |= BLOCK_SOLID;
             const int packed = (int)bx | ((int)by << 16);
+            int64_t own_fluid = 0;
+            for (int yy = std::max(0, y0); yy < std::min(ny, y0 + c->ty); ++yy)
+                for (int xx = std::max(0, x0); xx < std::min(nx, x0 + c->tx); ++xx)
+                    own_fluid += sol[(size_t)yy * nx + xx] ? 0 : 1;
+            (gen ? gen_nodes : fast_nodes_cnt) += own_fluid;
             if (gen) {
                 // face sides seen by the tile's psi halo (after the ghost mirror):
                 // each gets a strip of face nodes reconstructed once per tile
@@ -584,6 +591,8 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
         }
     c->nfast = (int)list_fast.size();
     c->ngeneral = (int)list_gen.size();
+    c->fast_nodes = fast_nodes_cnt;
+    c->general_nodes = gen_nodes;
     std::vector<int> blist(list_fast);
     blist.insert(blist.end(), list_gen.begin(), list_gen.end());
     std::vector<uint8_t> bflags(fl_fast);
@@ -1088,6 +1097,18 @@ lbm_status lbm_set_tile_variant(lbm_ctx* c, int variant) {
 }
 
 int lbm_num_tile_variants(void) { return d2q9_num_variants(); }
+
+lbm_status lbm_tile_stats(lbm_ctx* c, int* variant, int* fast_tiles, int* general_tiles, int64_t* fast_nodes,
+                          int64_t* general_nodes) {
+    if (!c || !variant || !fast_tiles || !general_tiles || !fast_nodes || !general_nodes)
+        return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    *variant = c->variant;
+    *fast_tiles = c->nfast;
+    *general_tiles = c->ngeneral;
+    *fast_nodes = c->fast_nodes;
+    *general_nodes = c->general_nodes;
+    return LBM_OK;
+}
 
 lbm_status lbm_set_graph_mode(lbm_ctx* c, int use_graphs) {
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");

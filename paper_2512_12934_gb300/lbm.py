@@ -108,6 +108,8 @@ def load():
     L.lbm_set_tile_variant.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_num_tile_variants.restype = ctypes.c_int
     L.lbm_num_tile_variants.argtypes = []
+    L.lbm_tile_stats.restype = ctypes.c_int
+    L.lbm_tile_stats.argtypes = [c_ctx] + [ctypes.POINTER(ctypes.c_int)] * 3 + [ctypes.POINTER(ctypes.c_int64)] * 2
     L.lbm_set_graph_mode.restype = ctypes.c_int
     L.lbm_set_graph_mode.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_mass_noalloc.restype = ctypes.c_int
@@ -255,6 +257,14 @@ class Solver:
 
     def set_tile_variant(self, v):
         _check(load().lbm_set_tile_variant(self.h, int(v)), self.h)
+
+    def tile_stats(self):
+        v, a, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        fn, gn = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().lbm_tile_stats(self.h, ctypes.byref(v), ctypes.byref(a), ctypes.byref(b), ctypes.byref(fn),
+                                     ctypes.byref(gn)), self.h)
+        return {"variant": v.value, "fast_tiles": a.value, "general_tiles": b.value,
+                "fast_nodes": fn.value, "general_nodes": gn.value}
 
     def set_graph_mode(self, on):
         _check(load().lbm_set_graph_mode(self.h, int(bool(on))), self.h)

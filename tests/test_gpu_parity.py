@@ -200,3 +200,39 @@ def test_tile_variants_and_graph_replay_agree(variant):
     q.set_graph_mode(0)
     q.step(70)
     assert rel_inf(p.macros()[1], q.macros()[1]) < 1e-5
+    st = p.tile_stats()
+    assert st["variant"] == variant
+    assert st["fast_nodes"] + st["general_nodes"] == int((c.solid == 0).sum())
+
+
+@pytest.mark.parametrize("workload", ["laplace", "channel"])
+def test_fp16_deviation_storage_error_is_bounded(workload, capsys):
+    """FP16 storage of f_i - w_i rho0 with FP32 arithmetic: error against the
+    FP64 oracle after 100 steps, stated per result.  The deviation from
+    w_i rho0 (rho0 = 1) is small for the major phase but close to -w_i for
+    the minor phase (rho ~ 0.001), whose density therefore carries the
+    half-precision rounding of a number of size w_i."""
+    if workload == "laplace":
+        w = W.laplace(G12=1.2)
+    else:
+        w = W.channel(nx=200, ny=40, R=8, xc=60, u_max=0.02, G12=1.6, Gw=(0.5, -0.5))
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u, threads=THREADS)
+    o.step(100)
+    s = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision="fp16store")
+    s.step(100)
+    ro, uo, _ = o.macros()
+    rg, ug = s.macros()
+    rt_o, rt_g = ro[0] + ro[1], rg[0] + rg[1]
+    major = np.maximum(ro[0], ro[1]) > 0.5
+    e_rho_total = rel_inf(rt_g, rt_o)
+    e_rho_major = np.max(np.abs(rg - ro)[:, major & (ro[0] > 0.5)]) if np.any(major) else 0.0
+    e_u = rel_inf(ug, uo)
+    minor = (ro > 0) & (ro < 0.01)
+    e_minor_abs = np.max(np.abs(rg - ro)[minor]) if np.any(minor) else 0.0
+    with capsys.disabled():
+        print("\n[fp16store %s] rho_total rel %.2e, major-phase rho abs %.2e, minor-phase rho abs %.2e, u rel %.2e"
+              % (workload, e_rho_total, e_rho_major, e_minor_abs, e_u))
+    assert np.all(np.isfinite(rg)) and np.all(np.isfinite(ug))
+    assert e_rho_total < 5e-3
+    assert e_minor_abs < 1e-3
+    assert e_u < 0.2
