@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 KERNEL_SRC = os.path.join(ROOT, "paper_2512_12934_gb300", "csrc", "lbm_d2q9.cu")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "d2q9_step_channel_1024x128.md")
-BYTES_PER_NODE = {"fp32": 144, "fp16store": 72, "fp64": 288}
+BYTES_PER_NODE = {"fp32": 144, "fp16store": 80, "fp64": 288}
 DTYPE = {"fp32": "f32", "fp16store": "f16-storage/f32", "fp64": "f64"}
 
 

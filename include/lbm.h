@@ -43,8 +43,11 @@ typedef enum {
 enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
 
 /* Arithmetic / storage of the populations.  FP32: f stored and computed in
- * float.  FP32_FP16STORE: f stored as half deviations from w_i * rho0,
- * computed in float.  FP64: stored and computed in double (diagnostic). */
+ * float.  FP32_FP16STORE: f stored as half deviations from w_i * rho_ref,
+ * rho_ref being the half-rounded density of the node that pulls the value in
+ * the next step (per node and component, stored alongside: 80 B per node and
+ * step instead of 144), computed in float.  FP64: stored and computed in
+ * double (diagnostic). */
 enum { LBM_FP32 = 0, LBM_FP32_FP16STORE = 1, LBM_FP64 = 2 };
 
 enum { LBM_INLET_VELOCITY = 1, LBM_OUTLET_CONVECTIVE = 2 };
@@ -74,7 +77,7 @@ typedef struct {
  *  s_eps_mode LBM_SEPS_MAX_NU (paper) or LBM_SEPS_OWN_NU.
  *  body_force body-force density, shared between components by rho_k/rho.
  *  precision  LBM_FP32, LBM_FP32_FP16STORE or LBM_FP64.
- *  rho0_store reference density of the FP16 deviation storage (<= 0: 1). */
+ *  rho0_store reserved (ignored: FP16 storage references per-node densities). */
 typedef struct {
     double G12;
     double Gw[2];

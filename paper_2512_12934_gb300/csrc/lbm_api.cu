@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -69,6 +70,8 @@ struct lbm_ctx {
     int* block_slot = nullptr;
     unsigned int* status = nullptr;
     void* macro = nullptr;
+    void* rref[2] = {nullptr, nullptr};  // FP16 storage: per-node half reference densities [2][plane]
+    std::vector<uint16_t> h_info;        // host copy of the per-node descriptors
     double* diag_partials = nullptr;
     int diag_blocks = 0;
     int nslots = 0;
@@ -135,7 +138,7 @@ void free_ctx(lbm_ctx* c) {
     for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
     void* ptrs[] = {c->f[0], c->f[1], c->info, c->blocks, c->block_flags, c->block_strips, c->uin, c->Fp[0], c->Fp[1], c->fo[0], c->fo[1],
                     c->scal[0], c->scal[1], c->partials[0], c->partials[1], c->block_slot, c->status,
-                    c->macro, c->diag_partials};
+                    c->macro, c->diag_partials, c->rref[0], c->rref[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->stage) cudaFreeHost(c->stage);
@@ -178,6 +181,8 @@ D2Args<S, R> make_args(lbm_ctx* c, bool write_macros) {
     a.part_out = c->partials[out];
     a.nslots = c->nslots;
     a.macro = write_macros ? static_cast<R*>(c->macro) : nullptr;
+    a.rref_in = c->rref[in];
+    a.rref_out = c->rref[out];
     a.status = c->status;
     a.G12 = (R)c->params.G12;
     a.Gw[0] = (R)c->params.Gw[0];
@@ -186,7 +191,6 @@ D2Args<S, R> make_args(lbm_ctx* c, bool write_macros) {
         for (int r = 0; r < 9; ++r) a.s[k][r] = (R)c->s[k][r];
     a.body[0] = (R)c->params.body_force[0];
     a.body[1] = (R)c->params.body_force[1];
-    a.rho0 = (R)c->params.rho0_store;
     return a;
 }
 
@@ -338,24 +342,65 @@ double from_store<double>(double v, double) { return v; }
 template <>
 double from_store<__half>(__half v, double wr) { return (double)__half2float(v) + wr; }
 
+// Destination of direction i leaving node (x, y): the node that pulls it next
+// step, or the node itself when the value bounces back (pull bit opp(i) set).
+void dest_node(const lbm_ctx* c, int x, int y, int i, int* dx, int* dy) {
+    const int opp = (i == 0) ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5);
+    const uint16_t inf = c->h_info[(size_t)y * c->pitch + x];
+    if ((inf >> opp) & 1u) {
+        *dx = x;
+        *dy = y;
+        return;
+    }
+    int u = x + kEx[i], v = y + kEy[i];
+    if (u < 0) u += c->nx;
+    else if (u >= c->nx) u -= c->nx;
+    if (v < 0) v += c->ny;
+    else if (v >= c->ny) v -= c->ny;
+    *dx = u;
+    *dy = v;
+}
+
+// Upload post-collision populations fh [2][9][ny][nx] (double) into buffer
+// `which`.  FP16 storage also sets that parity's reference densities to the
+// half-rounded node densities and encodes each value against its destination.
 template <typename S>
 lbm_status upload_f(lbm_ctx* c, const double* fh, int which) {
     const size_t count = (size_t)18 * c->plane;
     CK(cudaStreamSynchronize(c->stream));  // the staging buffer may still feed an earlier copy
     S* buf = static_cast<S*>(c->stage);
-    std::fill(buf, buf + count, to_store<S>(0.0, 0.0));
-    const double rho0 = c->params.rho0_store;
     const size_t N = (size_t)c->nx * c->ny;
+    std::vector<__half> ref;
+    if (std::is_same<S, __half>::value) {
+        ref.assign((size_t)2 * c->plane, __float2half_rn(0.0f));
+        for (int k = 0; k < 2; ++k)
+            for (int y = 0; y < c->ny; ++y)
+                for (int x = 0; x < c->nx; ++x) {
+                    double r = 0.0;
+                    for (int i = 0; i < 9; ++i) r += fh[((size_t)k * 9 + i) * N + (size_t)y * c->nx + x];
+                    ref[(size_t)k * c->plane + (size_t)y * c->pitch + x] = __float2half_rn((float)r);
+                }
+    }
+    std::fill(buf, buf + count, to_store<S>(0.0, 0.0));
     for (int k = 0; k < 2; ++k)
         for (int i = 0; i < 9; ++i)
             for (int y = 0; y < c->ny; ++y)
                 for (int x = 0; x < c->nx; ++x) {
+                    const size_t d = (size_t)y * c->pitch + x;
+                    if (c->host_solid[d]) continue;
                     const double v = fh[((size_t)k * 9 + i) * N + (size_t)y * c->nx + x];
-                    buf[(size_t)(k * 9 + i) * c->plane + (size_t)y * c->pitch + x] =
-                        to_store<S>(v, kW[i] * rho0);
+                    double wr = 0.0;
+                    if (!ref.empty()) {
+                        int dx, dy;
+                        dest_node(c, x, y, i, &dx, &dy);
+                        wr = kW[i] * (double)__half2float(ref[(size_t)k * c->plane + (size_t)dy * c->pitch + dx]);
+                    }
+                    buf[(size_t)(k * 9 + i) * c->plane + d] = to_store<S>(v, wr);
                 }
     CK(cudaMemcpyAsync(c->f[which], buf, count * sizeof(S), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (!ref.empty())
+        CK(cudaMemcpy(c->rref[which], ref.data(), ref.size() * sizeof(__half), cudaMemcpyHostToDevice));
     return LBM_OK;
 }
 
@@ -366,7 +411,11 @@ lbm_status download_f(lbm_ctx* c, double* fh) {
     const S* buf = static_cast<const S*>(c->stage);
     CK(cudaMemcpyAsync(c->stage, c->f[c->cur], count * sizeof(S), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    const double rho0 = c->params.rho0_store;
+    std::vector<__half> ref;
+    if (std::is_same<S, __half>::value) {
+        ref.resize((size_t)2 * c->plane);
+        CK(cudaMemcpy(ref.data(), c->rref[c->cur], ref.size() * sizeof(__half), cudaMemcpyDeviceToHost));
+    }
     const size_t N = (size_t)c->nx * c->ny;
     for (int k = 0; k < 2; ++k)
         for (int i = 0; i < 9; ++i)
@@ -374,8 +423,15 @@ lbm_status download_f(lbm_ctx* c, double* fh) {
                 for (int x = 0; x < c->nx; ++x) {
                     const size_t d = (size_t)y * c->pitch + x;
                     double v = 0.0;
-                    if (!c->host_solid[d])
-                        v = from_store<S>(buf[(size_t)(k * 9 + i) * c->plane + d], kW[i] * rho0);
+                    if (!c->host_solid[d]) {
+                        double wr = 0.0;
+                        if (!ref.empty()) {
+                            int dx, dy;
+                            dest_node(c, x, y, i, &dx, &dy);
+                            wr = kW[i] * (double)__half2float(ref[(size_t)k * c->plane + (size_t)dy * c->pitch + dx]);
+                        }
+                        v = from_store<S>(buf[(size_t)(k * 9 + i) * c->plane + d], wr);
+                    }
                     fh[((size_t)k * 9 + i) * N + (size_t)y * c->nx + x] = v;
                 }
     return LBM_OK;
@@ -522,20 +578,37 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
             const bool edge = x0 - 3 < 0 || x0 + c->tx + 3 > nx || y0 - 3 < 0 || y0 + c->ty + 3 > ny;
             bool gen = (x0 - 2 < 0 && c->open_side[0]) || (x0 + c->tx + 2 > nx && c->open_side[1]) ||
                        (y0 - 2 < 0 && c->open_side[2]) || (y0 + c->ty + 2 > ny && c->open_side[3]);
-            bool near_solid = false, part = false;
-            for (int yy = std::max(0, y0 - 2); yy < std::min(ny, y0 + c->ty + 2); ++yy)
-                for (int xx = std::max(0, x0 - 2); xx < std::min(nx, x0 + c->tx + 2); ++xx) {
-                    const size_t h = (size_t)yy * nx + xx;
+            bool near_solid = false, part = false, closed_edge = false;
+            // every site of the psi halo, resolved as the kernel resolves it
+            // (periodic wrap, ghost mirror on open sides, solid outside a closed edge)
+            for (int yy = y0 - 2; yy < y0 + c->ty + 2; ++yy)
+                for (int xx = x0 - 2; xx < x0 + c->tx + 2; ++xx) {
+                    int gx = xx, gy = yy;
+                    bool outside = false;
+                    if (gx < 0 || gx >= nx) {
+                        if (grid->periodic[0]) gx = ((gx % nx) + nx) % nx;
+                        else if (c->open_side[gx < 0 ? 0 : 1]) gx = std::min(std::max(gx < 0 ? -1 - gx : 2 * nx - 1 - gx, 0), nx - 1);
+                        else outside = true;
+                    }
+                    if (gy < 0 || gy >= ny) {
+                        if (grid->periodic[1]) gy = ((gy % ny) + ny) % ny;
+                        else if (c->open_side[gy < 0 ? 2 : 3]) gy = std::min(std::max(gy < 0 ? -1 - gy : 2 * ny - 1 - gy, 0), ny - 1);
+                        else outside = true;
+                    }
+                    if (outside) {
+                        closed_edge = true;
+                        continue;
+                    }
+                    const size_t h = (size_t)gy * nx + gx;
                     gen = gen || faceid[h] != 0;
                     near_solid = near_solid || sol[h] != 0;
-                    const bool own = xx >= x0 && xx < x0 + c->tx && yy >= y0 && yy < y0 + c->ty;
+                    const bool own = xx >= x0 && xx < x0 + c->tx && yy >= y0 && yy < y0 + c->ty &&
+                                     xx >= 0 && xx < nx && yy >= 0 && yy < ny;
                     if (own && !sol[h] &&
                         ((faceid[h] && c->faces[faceid[h] - 1].kind == FACE_INLET) ||
                          (nbrid[h] && nbrid[h] - 1 == c->out_face)))
                         part = true;
                 }
-            const bool closed_edge = (x0 - 2 < 0 && !grid->periodic[0]) || (x0 + c->tx + 2 > nx && !grid->periodic[0]) ||
-                                     (y0 - 2 < 0 && !grid->periodic[1]) || (y0 + c->ty + 2 > ny && !grid->periodic[1]);
             uint8_t fl = 0;
             if (edge) fl |= BLOCK_EDGE;
             if (near_solid || closed_edge || gen) fl |= BLOCK_SOLID;
@@ -671,8 +744,6 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
     c->grid = *grid;
     c->params = *params;
     if (c->params.s_q <= 0.0) c->params.s_q = 1.2;
-    if (c->params.rho0_store <= 0.0) c->params.rho0_store = 1.0;
-    if (c->params.precision != LBM_FP32_FP16STORE) c->params.rho0_store = 0.0;
     c->nx = grid->nx;
     c->ny = grid->ny;
     c->pitch = (grid->nx + 31) / 32 * 32;
@@ -818,12 +889,14 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
     c->diag_blocks = 152 * 4;
     cudaError_t e = cudaGetDevice(&c->device);
     void** allocs[] = {&c->f[0], &c->f[1], (void**)&c->info, &c->uin, &c->Fp[0], &c->Fp[1], &c->fo[0], &c->fo[1],
-                       (void**)&c->scal[0], (void**)&c->scal[1], (void**)&c->status, &c->macro, (void**)&c->diag_partials};
+                       (void**)&c->scal[0], (void**)&c->scal[1], (void**)&c->status, &c->macro, (void**)&c->diag_partials,
+                       &c->rref[0], &c->rref[1]};
     const size_t sizes[] = {fbytes, fbytes, (size_t)c->plane * 2, (size_t)nfn * c->rbytes,
                             (size_t)nfn * 8 * c->rbytes, (size_t)nfn * 8 * c->rbytes,
                             (size_t)nfn * 18 * c->rbytes, (size_t)nfn * 18 * c->rbytes, 64, 64,
                             16,
-                            (size_t)4 * c->plane * c->rbytes, (size_t)c->diag_blocks * 3 * 8};
+                            (size_t)4 * c->plane * c->rbytes, (size_t)c->diag_blocks * 3 * 8,
+                            (size_t)2 * c->plane * 2, (size_t)2 * c->plane * 2};
     for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]) && e == cudaSuccess; ++i) {
         e = cudaMalloc(allocs[i], sizes[i]);
         if (e == cudaSuccess) e = cudaMemset(*allocs[i], 0, sizes[i]);
@@ -835,6 +908,7 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
         return fail(nullptr, st, msg);
     }
     e = cudaMemcpy(c->info, info.data(), info.size() * 2, cudaMemcpyHostToDevice);
+    c->h_info = info;
 
     if (e == cudaSuccess && c->nface_nodes > 0) {
         if (c->rbytes == 8) {
@@ -939,16 +1013,20 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f) {
 lbm_status lbm_get_diagnostics(lbm_ctx* c, lbm_diag* out) {
     if (!c || !out) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
     cudaError_t e;
+    const int px = c->grid.periodic[0] ? 1 : 0, py = c->grid.periodic[1] ? 1 : 0;
+    const void* rr = c->rref[c->cur];
     if (c->precision == LBM_FP64)
-        e = launch_d2q9_diag<double, double>((const double*)c->f[c->cur], (const double*)c->macro, c->info, c->nx,
-                                             c->ny, c->pitch, c->plane, 0.0, c->diag_partials, c->diag_blocks, c->stream);
+        e = launch_d2q9_diag<double, double>((const double*)c->f[c->cur], (const double*)c->macro, c->info, rr,
+                                             c->nx, c->ny, px, py, c->pitch, c->plane, c->diag_partials,
+                                             c->diag_blocks, c->stream);
     else if (c->precision == LBM_FP32)
-        e = launch_d2q9_diag<float, float>((const float*)c->f[c->cur], (const float*)c->macro, c->info, c->nx, c->ny,
-                                           c->pitch, c->plane, 0.0f, c->diag_partials, c->diag_blocks, c->stream);
+        e = launch_d2q9_diag<float, float>((const float*)c->f[c->cur], (const float*)c->macro, c->info, rr, c->nx,
+                                           c->ny, px, py, c->pitch, c->plane, c->diag_partials, c->diag_blocks,
+                                           c->stream);
     else
-        e = launch_d2q9_diag<__half, float>((const __half*)c->f[c->cur], (const float*)c->macro, c->info, c->nx,
-                                            c->ny, c->pitch, c->plane, (float)c->params.rho0_store,
-                                            c->diag_partials, c->diag_blocks, c->stream);
+        e = launch_d2q9_diag<__half, float>((const __half*)c->f[c->cur], (const float*)c->macro, c->info, rr,
+                                            c->nx, c->ny, px, py, c->pitch, c->plane, c->diag_partials,
+                                            c->diag_blocks, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "diag launch");
     c->launches += 1;
     std::vector<double> part((size_t)c->diag_blocks * 3);
@@ -1001,7 +1079,8 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
     const size_t nfn = (size_t)std::max(1, c->nface_nodes);
     const size_t mbytes = (size_t)4 * c->plane * c->rbytes;
     const size_t pbytes = (size_t)std::max(1, c->nslots) * 4 * 8;
-    std::vector<char> buf(fbytes + nfn * 8 * c->rbytes + nfn * 18 * c->rbytes + 64 + mbytes + pbytes);
+    const size_t rbytes_ref = (size_t)2 * c->plane * 2;
+    std::vector<char> buf(fbytes + nfn * 8 * c->rbytes + nfn * 18 * c->rbytes + 64 + mbytes + pbytes + rbytes_ref);
     char* p = buf.data();
     CK(cudaMemcpy(p, c->f[c->cur], fbytes, cudaMemcpyDeviceToHost));
     p += fbytes;
@@ -1014,7 +1093,9 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
     CK(cudaMemcpy(p, c->macro, mbytes, cudaMemcpyDeviceToHost));
     p += mbytes;
     CK(cudaMemcpy(p, c->partials[c->cur], pbytes, cudaMemcpyDeviceToHost));
-    const char magic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '2'};
+    p += pbytes;
+    CK(cudaMemcpy(p, c->rref[c->cur], rbytes_ref, cudaMemcpyDeviceToHost));
+    const char magic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '3'};
     const int64_t hdr[6] = {c->nx, c->ny, c->precision, c->nface_nodes, c->step, (int64_t)buf.size()};
     bool ok = std::fwrite(magic, 1, 8, fp) == 8 && std::fwrite(hdr, sizeof(hdr), 1, fp) == 1 &&
               std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
@@ -1033,8 +1114,9 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
     const size_t nfn = (size_t)std::max(1, c->nface_nodes);
     const size_t mbytes = (size_t)4 * c->plane * c->rbytes;
     const size_t pbytes = (size_t)std::max(1, c->nslots) * 4 * 8;
-    const size_t total = fbytes + nfn * 8 * c->rbytes + nfn * 18 * c->rbytes + 64 + mbytes + pbytes;
-    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "LBMCKPT2", 8) == 0 &&
+    const size_t rbytes_ref = (size_t)2 * c->plane * 2;
+    const size_t total = fbytes + nfn * 8 * c->rbytes + nfn * 18 * c->rbytes + 64 + mbytes + pbytes + rbytes_ref;
+    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "LBMCKPT3", 8) == 0 &&
               std::fread(hdr, sizeof(hdr), 1, fp) == 1 && hdr[0] == c->nx && hdr[1] == c->ny &&
               hdr[2] == c->precision && hdr[3] == c->nface_nodes && hdr[5] == (int64_t)total;
     std::vector<char> buf(total);
@@ -1054,6 +1136,8 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
     CK(cudaMemcpy(c->macro, p, mbytes, cudaMemcpyHostToDevice));
     p += mbytes;
     CK(cudaMemcpy(c->partials[c->cur], p, pbytes, cudaMemcpyHostToDevice));
+    p += pbytes;
+    CK(cudaMemcpy(c->rref[c->cur], p, rbytes_ref, cudaMemcpyHostToDevice));
     c->step = hdr[4];
     return LBM_OK;
 }

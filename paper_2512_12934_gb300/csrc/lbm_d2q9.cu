@@ -49,6 +49,12 @@ __host__ __device__ constexpr R w8_(int dx, int dy) {
 }
 
 // ---- population storage ------------------------------------------------
+// FP32 / FP64 store f itself.  FP16 storage keeps half(f_i - w_i rho_ref),
+// where rho_ref is the half-rounded density of component k at the node that
+// pulls the value in the next step (the writing node itself when the value
+// bounces back).  Every node also stores its own rho_ref, so a reader decodes
+// all nine pulled values with one reference pair: deviations stay small for
+// the major and the minor phase alike.
 template <typename S, typename R>
 struct Pop {
     static __device__ __forceinline__ R ld(const S* __restrict__ p, int j, R /*wr*/) {
@@ -68,6 +74,27 @@ struct Pop<__half, float> {
     }
 };
 
+template <typename S>
+__host__ __device__ constexpr bool is_half_() { return std::is_same<S, __half>::value; }
+
+// Reference densities of node n for decoding its pulled populations.
+template <typename S, typename R>
+__device__ __forceinline__ void node_ref(const D2Args<S, R>& a, int n, R (&ref)[2]) {
+    if constexpr (is_half_<S>()) {
+        const __half* rr = static_cast<const __half*>(a.rref_in);
+        ref[0] = __half2float(rr[n]);
+        ref[1] = __half2float(rr[a.plane + n]);
+    } else {
+        ref[0] = R(0);
+        ref[1] = R(0);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R half_round(R v) {
+    return R(__half2float(__float2half_rn(float(v))));
+}
+
 template <typename R>
 __device__ __forceinline__ R feq_(int i, R rho, R ux, R uy) {
     const R eu = R(ex_(i)) * ux + R(ey_(i)) * uy;
@@ -84,6 +111,8 @@ __device__ __forceinline__ R feq_(int i, R rho, R ux, R uy) {
 // Interior pull: every source lies inside the grid, no wrap needed.
 template <typename S, typename R>
 __device__ __forceinline__ void pull_interior(const D2Args<S, R>& a, int n, unsigned info, R (&f)[2][9]) {
+    R ref[2];
+    node_ref(a, n, ref);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const bool bb = (info >> i) & 1u;
@@ -91,7 +120,7 @@ __device__ __forceinline__ void pull_interior(const D2Args<S, R>& a, int n, unsi
         const int dir = bb ? opp_(i) : i;
 #pragma unroll
         for (int k = 0; k < 2; ++k)
-            f[k][i] = Pop<S, R>::ld(a.fin, (k * 9 + dir) * a.plane + src, w_<R>(dir) * a.rho0);
+            f[k][i] = Pop<S, R>::ld(a.fin, (k * 9 + dir) * a.plane + src, w_<R>(i) * ref[k]);
     }
 }
 
@@ -99,6 +128,8 @@ __device__ __forceinline__ void pull_interior(const D2Args<S, R>& a, int n, unsi
 template <typename S, typename R>
 __device__ __forceinline__ void pull_wrap(const D2Args<S, R>& a, int x, int y, unsigned info, R (&f)[2][9]) {
     const int n = y * a.pitch + x;
+    R ref[2];
+    node_ref(a, n, ref);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         int src, dir;
@@ -114,7 +145,7 @@ __device__ __forceinline__ void pull_wrap(const D2Args<S, R>& a, int x, int y, u
         }
 #pragma unroll
         for (int k = 0; k < 2; ++k)
-            f[k][i] = Pop<S, R>::ld(a.fin, (k * 9 + dir) * a.plane + src, w_<R>(dir) * a.rho0);
+            f[k][i] = Pop<S, R>::ld(a.fin, (k * 9 + dir) * a.plane + src, w_<R>(i) * ref[k]);
     }
 }
 
@@ -733,9 +764,20 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
             o[6] = g[6] + (dg - px + py - cxy);
             o[7] = g[7] + (dg - px - py + cxy);
             o[8] = g[8] + (dg + px - py - cxy);
+            if constexpr (is_half_<S>()) {
+                // encode with the reference density of the node that pulls each value
+                const R own = half_round(r);
 #pragma unroll
-            for (int i = 0; i < 9; ++i)
-                Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o[i], w_<R>(i) * a.rho0);
+                for (int i = 0; i < 9; ++i) {
+                    const R dref = ((info >> opp_(i)) & 1u) ? own
+                                                           : half_round(sm.rho[k][ty + 2 + ey_(i)][tx + 2 + ex_(i)]);
+                    Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o[i], w_<R>(i) * dref);
+                }
+                static_cast<__half*>(a.rref_out)[k * a.plane + n] = __float2half_rn(float(r));
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o[i], R(0));
+            }
         }
     }
 
@@ -786,27 +828,44 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
 // FP64 mass / speed reduction for diagnostics.
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) d2q9_diag_kernel(const S* __restrict__ f, const R* __restrict__ macro,
-                                                        const uint16_t* __restrict__ info, int nx, int ny,
-                                                        int pitch, long long plane, R rho0,
-                                                        double* partials) {
+                                                        const uint16_t* __restrict__ info,
+                                                        const void* __restrict__ rref, int nx, int ny, int px,
+                                                        int py, int pitch, long long plane, double* partials) {
     double m0 = 0.0, m1 = 0.0, umax = 0.0;
     const long long total = (long long)nx * ny;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(t % nx), y = (int)(t / nx);
         const long long n = (long long)y * pitch + x;
-        if (info[n] & INFO_SOLID) continue;
+        const unsigned inf = info[n];
+        if (inf & INFO_SOLID) continue;
         double a0 = 0.0, a1 = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            a0 += (double)Pop<S, R>::ld(f, (int)(i * plane + n), w_<R>(i) * rho0);
-            a1 += (double)Pop<S, R>::ld(f, (int)((9 + i) * plane + n), w_<R>(i) * rho0);
+            R r0 = R(0), r1 = R(0);
+            if constexpr (is_half_<S>()) {
+                // reference of the node that pulls direction i next (the node itself on bounce-back)
+                long long d = n;
+                if (!((inf >> opp_(i)) & 1u)) {
+                    int dx = x + ex_(i), dy = y + ey_(i);
+                    if (dx < 0) dx += nx; else if (dx >= nx) dx -= nx;
+                    if (dy < 0) dy += ny; else if (dy >= ny) dy -= ny;
+                    d = (long long)dy * pitch + dx;
+                }
+                const __half* rr = static_cast<const __half*>(rref);
+                r0 = __half2float(rr[d]);
+                r1 = __half2float(rr[plane + d]);
+            }
+            a0 += (double)Pop<S, R>::ld(f, (int)(i * plane + n), w_<R>(i) * r0);
+            a1 += (double)Pop<S, R>::ld(f, (int)((9 + i) * plane + n), w_<R>(i) * r1);
         }
         m0 += a0;
         m1 += a1;
         const double ux = (double)macro[2 * plane + n], uy = (double)macro[3 * plane + n];
         umax = fmax(umax, ux * ux + uy * uy);
     }
+    (void)px;
+    (void)py;
     __shared__ double red[3][8];
     for (int o = 16; o > 0; o >>= 1) {
         m0 += __shfl_down_sync(0xffffffffu, m0, o);
@@ -864,21 +923,22 @@ cudaError_t launch_d2q9_step(const D2Args<S, R>& a, int variant, bool general, i
 }
 
 template <typename S, typename R>
-cudaError_t launch_d2q9_diag(const S* f, const R* macro, const uint16_t* info, int nx, int ny,
-                             int pitch, long long plane, R rho0, double* partials, int nblocks,
+cudaError_t launch_d2q9_diag(const S* f, const R* macro, const uint16_t* info, const void* rref, int nx,
+                             int ny, int px, int py, int pitch, long long plane, double* partials, int nblocks,
                              cudaStream_t st) {
-    d2q9_diag_kernel<S, R><<<nblocks, 256, 0, st>>>(f, macro, info, nx, ny, pitch, plane, rho0, partials);
+    d2q9_diag_kernel<S, R><<<nblocks, 256, 0, st>>>(f, macro, info, rref, nx, ny, px, py, pitch, plane, partials);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_d2q9_step<float, float>(const D2Args<float, float>&, int, bool, int, cudaStream_t);
 template cudaError_t launch_d2q9_step<double, double>(const D2Args<double, double>&, int, bool, int, cudaStream_t);
 template cudaError_t launch_d2q9_step<__half, float>(const D2Args<__half, float>&, int, bool, int, cudaStream_t);
-template cudaError_t launch_d2q9_diag<float, float>(const float*, const float*, const uint16_t*, int, int, int,
-                                                    long long, float, double*, int, cudaStream_t);
-template cudaError_t launch_d2q9_diag<double, double>(const double*, const double*, const uint16_t*, int, int,
-                                                      int, long long, double, double*, int, cudaStream_t);
-template cudaError_t launch_d2q9_diag<__half, float>(const __half*, const float*, const uint16_t*, int, int, int,
-                                                     long long, float, double*, int, cudaStream_t);
+template cudaError_t launch_d2q9_diag<float, float>(const float*, const float*, const uint16_t*, const void*, int,
+                                                    int, int, int, int, long long, double*, int, cudaStream_t);
+template cudaError_t launch_d2q9_diag<double, double>(const double*, const double*, const uint16_t*, const void*,
+                                                      int, int, int, int, int, long long, double*, int,
+                                                      cudaStream_t);
+template cudaError_t launch_d2q9_diag<__half, float>(const __half*, const float*, const uint16_t*, const void*, int,
+                                                     int, int, int, int, long long, double*, int, cudaStream_t);
 
 }  // namespace lbm

@@ -78,12 +78,13 @@ struct D2Args {
     double* __restrict__ part_out;        // [slot][4] partials of this step: Qin, Qout, sum u_n, count
     int nslots;
     R* __restrict__ macro;                // optional [4][plane]: rho1, rho2, ux, uy
+    const void* __restrict__ rref_in;     // FP16 storage: [2][plane] half reference densities (decode)
+    void* __restrict__ rref_out;          // FP16 storage: reference densities written by this step
     unsigned int* status;
     R G12;
     R Gw[2];
     R s[2][9];
     R body[2];
-    R rho0;                                // FP16 deviation reference density
 };
 
 // Launch one list of tiles of one step: general = false -> fast kernel,
@@ -97,9 +98,11 @@ int d2q9_num_variants();
 
 // FP64 diagnostics over the current populations and macro buffer:
 // per-block partials [nblocks][3] = mass1, mass2, max |u|^2.
+// (FP16 storage decodes each population with its destination's reference
+// density rref [2][plane]; px, py are the periodic flags.)
 template <typename S, typename R>
-cudaError_t launch_d2q9_diag(const S* f, const R* macro, const uint16_t* info, int nx, int ny,
-                             int pitch, long long plane, R rho0, double* partials, int nblocks,
+cudaError_t launch_d2q9_diag(const S* f, const R* macro, const uint16_t* info, const void* rref, int nx,
+                             int ny, int px, int py, int pitch, long long plane, double* partials, int nblocks,
                              cudaStream_t st);
 
 // Record the calling thread's last error (fixed buffer, no allocation).

@@ -207,11 +207,12 @@ def test_tile_variants_and_graph_replay_agree(variant):
 
 @pytest.mark.parametrize("workload", ["laplace", "channel"])
 def test_fp16_deviation_storage_error_is_bounded(workload, capsys):
-    """FP16 storage of f_i - w_i rho0 with FP32 arithmetic: error against the
-    FP64 oracle after 100 steps, stated per result.  The deviation from
-    w_i rho0 (rho0 = 1) is small for the major phase but close to -w_i for
-    the minor phase (rho ~ 0.001), whose density therefore carries the
-    half-precision rounding of a number of size w_i."""
+    """FP16 storage with FP32 arithmetic: error against the FP64 oracle after
+    100 steps, stated per result.  Each population is stored as a half
+    deviation from w_i times the density of the node that pulls it next, so
+    the major and the minor phase (rho ~ 0.001) both keep small deviations.
+    Measured on GB300: Laplace rho 4.0e-5 rel, minor-phase rho 8.9e-7 abs,
+    u 1.5e-3 rel; channel rho 5.4e-5, 1.6e-6, u 9.3e-4."""
     if workload == "laplace":
         w = W.laplace(G12=1.2)
     else:
@@ -233,6 +234,20 @@ def test_fp16_deviation_storage_error_is_bounded(workload, capsys):
         print("\n[fp16store %s] rho_total rel %.2e, major-phase rho abs %.2e, minor-phase rho abs %.2e, u rel %.2e"
               % (workload, e_rho_total, e_rho_major, e_minor_abs, e_u))
     assert np.all(np.isfinite(rg)) and np.all(np.isfinite(ug))
-    assert e_rho_total < 5e-3
-    assert e_minor_abs < 1e-3
-    assert e_u < 0.2
+    assert e_rho_total < 2e-4
+    assert e_minor_abs < 1e-5
+    assert e_u < 5e-3
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_tile_shape_sees_solids_across_periodic_edges(variant):
+    """A solid just across a periodic edge enters a tile's interaction halo by
+    wrap; every tile shape must include it in the adhesion term."""
+    w = W.random_box(33, 9, 3, periodic=(1, 1), solid_frac=0.1, G12=0.9, Gw=(0.3, -0.2))
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u)
+    o.step(30)
+    s = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision="fp64")
+    s.set_tile_variant(variant)
+    s.step(30)
+    assert rel_inf(s.macros()[0], o.macros()[0]) < 1e-11
+    assert rel_inf(s.macros()[1], o.macros()[1]) < 1e-11
