@@ -41,8 +41,11 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--lbm-steps", type=int, default=5000, help="LBM time steps per benchmark step")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16store", "fp64"])
-    p.add_argument("--workload", default="channel", choices=["channel", "channel_hbm"],
-                   help="channel: the 1024x128 config; channel_hbm: the same physics on 8192x2048")
+    p.add_argument("--workload", default="channel", choices=["channel", "channel_hbm", "tjunction_batch"],
+                   help="channel: the 1024x128 config; channel_hbm: the same physics on 8192x2048; "
+                        "tjunction_batch: the T-junction ensemble, batched vs sequential")
+    p.add_argument("--instances", type=int, default=256, help="ensemble size for tjunction_batch")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched-ensemble entry of the default line")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-hbm", action="store_true")
@@ -148,6 +151,56 @@ def cpu_oracle_sample(w, seconds, threads, min_steps=1):
     return w.fluid_nodes * steps / el / 1e6, steps, el
 
 
+def batched_vs_sequential(n, steps, reps, precision, stream_handle):
+    """Aggregate MLUPS of an n-instance T-junction ensemble stepped as one
+    autotuned batch, against the same instances stepped one after another
+    (each replaying its own captured graphs)."""
+    import torch
+
+    from paper_2512_12934_gb300 import lbm
+    from paper_2512_12934_gb300 import workloads as W
+
+    ens = W.tjunction_ensemble(n)
+    solvers = [lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision=precision, stream=stream_handle) for w in ens]
+    fluid = sum(w.fluid_nodes for w in ens)
+    batch = lbm.Batch(solvers, stream=stream_handle)
+    variant, tuned_ms = batch.autotune(steps=8)
+    batch.step(steps)
+    batch.sync()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(reps):
+        batch.step(steps)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_batch = ev0.elapsed_time(ev1) / 1e3
+    info = batch.info()
+    batch.close()
+    for sv in solvers:              # per-instance graphs captured outside the clock
+        sv.set_tile_variant(variant)
+        sv.step(steps)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        for sv in solvers:
+            sv.step(steps)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_seq = ev0.elapsed_time(ev1) / 1e3
+    status = max(sv.diagnostics()["status"] for sv in solvers)
+    for sv in solvers:
+        sv.close()
+    mb = fluid * steps * reps / t_batch / 1e6
+    ms = fluid * steps * reps / t_seq / 1e6
+    return {"instances": n, "fluid_nodes": fluid, "lbm_steps": steps * reps, "tile_variant": variant,
+            "fast_tiles": info["fast_tiles"], "general_tiles": info["general_tiles"],
+            "batched_mlups": mb, "sequential_mlups": ms, "speedup": mb / ms,
+            "batched_ms_per_step": t_batch / (steps * reps) * 1e3,
+            "roofline_frac_of_measured_hbm": mb * 1e6 * BYTES_PER_NODE[precision] / (measured_peaks()[0] * 1e9),
+            "status": status}
+
+
 def run_reference(args, world, rank):
     from paper_2512_12934_gb300 import workloads as W
 
@@ -211,6 +264,21 @@ def main():
 
     lbm.load()
     stream = torch.cuda.current_stream()
+    if args.workload == "tjunction_batch":
+        ck = Clocks(local)
+        ck.start()
+        res = batched_vs_sequential(args.instances, args.lbm_steps, args.steps, args.precision, stream.cuda_stream)
+        clk = ck.stop()
+        if rank == 0:
+            print(json.dumps({"metric": "MLUPS", "value": res["batched_mlups"], "unit": "MLUPS", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": res["batched_ms_per_step"] * args.lbm_steps,
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                              "dtype": DTYPE[args.precision], "data": "synthetic",
+                              "config": {"workload": "tjunction_ensemble_batched", "instances": args.instances,
+                                         "lbm_steps_per_step": args.lbm_steps, "precision": args.precision},
+                              "batched_ensemble": res, "clocks": clk}))
+        return 0
     w = W.channel() if args.workload == "channel" else W.channel(nx=8192, ny=2048, R=240, xc=1600)
     S = args.lbm_steps
     solver = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision=args.precision, stream=stream.cuda_stream)
@@ -323,6 +391,10 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "lbm_reset(host fields) + lbm_step + lbm_get_macros(host)"}
 
+    batched = None
+    if not args.no_batch and args.workload == "channel":
+        batched = batched_vs_sequential(64, 64, 3, args.precision, stream.cuda_stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         threads = os.cpu_count() or 1
@@ -345,6 +417,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
             "roofline": roofline,
             "roofline_hbm_resident": hbm,
+            "batched_ensemble": batched,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -246,6 +246,52 @@ lbm_status lbm_set_graph_mode(lbm_ctx* ctx, int use_graphs);
 lbm_status lbm_mass_noalloc(const void* f, int precision, int nx, int ny, int pitch,
                             const uint8_t* solid, double* mass, void* cuda_stream);
 
+/* ---- Batched ensembles (many independent instances, one launch per tile
+ * list per step for all of them) ----------------------------------------
+ * The paper runs one case at a time; batching is how many parameter points
+ * (uneven grids, faces and parameters) share the GPU.  A batch refers to
+ * existing contexts (the members, created with lbm_create, all of one
+ * precision); the caller keeps owning them and may still read them between
+ * batch steps (lbm_get_macros, lbm_get_diagnostics, ...).  Every member takes
+ * the batch's tile variant.  A batch step advances every member by one time
+ * step with exactly the arithmetic of lbm_step on that member alone. */
+typedef struct lbm_batch lbm_batch;
+
+/* members: n >= 1 distinct contexts of one precision; cuda_stream: the stream
+ * batch work is enqueued on (NULL = legacy default stream). */
+lbm_status lbm_batch_create(lbm_ctx* const* members, int n, void* cuda_stream, lbm_batch** out);
+
+/* Enqueue nsteps steps of every member (runs of 32 steps replay captured
+ * CUDA graphs); members' macroscopic fields are written by the last one. */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
+
+/* Wait for the batch stream; LBM_ERR_DIVERGED if any member diverged. */
+lbm_status lbm_batch_sync(lbm_batch* b);
+
+/* Re-tile every member with `variant` (see lbm_set_tile_variant). */
+lbm_status lbm_batch_set_tile_variant(lbm_batch* b, int variant);
+
+/* Autotuner: times `steps` batch steps of every tile variant from the
+ * current state (restored afterwards, so the run is unchanged) and keeps the
+ * fastest.  variant: the choice; ms_per_step (may be NULL): its time. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int steps, int* variant, double* ms_per_step);
+
+/* The same for a single context. */
+lbm_status lbm_autotune(lbm_ctx* ctx, int steps, int* variant, double* ms_per_step);
+
+/* Tile variant, number of tiles in the batch's fast and general lists and
+ * kernel launches issued by the batch so far. */
+lbm_status lbm_batch_info(lbm_batch* b, int* variant, int* fast_tiles, int* general_tiles, int64_t* launches);
+
+/* CUDA-graph replay on (default) or off for batch steps. */
+lbm_status lbm_batch_set_graph_mode(lbm_batch* b, int use_graphs);
+
+/* Release the batch (not its members).  NULL is ignored. */
+void lbm_batch_destroy(lbm_batch* b);
+
+/* Message of the batch's last failure (b == NULL: the thread's last). */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* Release all device memory of the context.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);
 

@@ -62,6 +62,7 @@ struct lbm_ctx {
     unsigned* block_strips = nullptr;
     int nfast = 0, ngeneral = 0;
     int64_t fast_nodes = 0, general_nodes = 0;  // fluid nodes owned by each tile list
+    int64_t tiling_gen = 0;                      // bumped whenever the tile lists are rebuilt
     void* uin = nullptr;
     void* Fp[2] = {nullptr, nullptr};
     void* fo[2] = {nullptr, nullptr};
@@ -146,9 +147,9 @@ void free_ctx(lbm_ctx* c) {
 }
 
 template <typename S, typename R>
-D2Args<S, R> make_args(lbm_ctx* c, bool write_macros) {
+D2Args<S, R> make_args_par(lbm_ctx* c, int in, bool write_macros) {
     D2Args<S, R> a{};
-    const int in = c->cur, out = 1 - c->cur;
+    const int out = 1 - in;
     a.nx = c->nx;
     a.ny = c->ny;
     a.pitch = c->pitch;
@@ -192,6 +193,11 @@ D2Args<S, R> make_args(lbm_ctx* c, bool write_macros) {
     a.body[0] = (R)c->params.body_force[0];
     a.body[1] = (R)c->params.body_force[1];
     return a;
+}
+
+template <typename S, typename R>
+D2Args<S, R> make_args(lbm_ctx* c, bool write_macros) {
+    return make_args_par<S, R>(c, c->cur, write_macros);
 }
 
 // Both tile lists of one step.  side != nullptr: the general list runs on a
@@ -537,6 +543,28 @@ lbm_status init_state(lbm_ctx* c, const double* rho_init, const double* u_init, 
     return LBM_OK;
 }
 
+// lambda / chi the next step would compute from the live partials, written
+// into the current scalar block as its initial values (valid flag cleared).
+lbm_status fold_partials(lbm_ctx* c) {
+    double sc[8];
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(sc, c->scal[c->cur], sizeof(sc), cudaMemcpyDeviceToHost));
+    if (sc[5] == 0.0 || c->nslots == 0) return LBM_OK;
+    std::vector<double> pp((size_t)c->nslots * 4);
+    CK(cudaMemcpy(pp.data(), c->partials[c->cur], pp.size() * 8, cudaMemcpyDeviceToHost));
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int sl = 0; sl < c->nslots; ++sl)
+        for (int j = 0; j < 4; ++j) t[j] += pp[(size_t)sl * 4 + j];
+    if (c->out_face >= 0 && t[3] > 0.0) {
+        const double um = t[2] / t[3];
+        sc[0] = um > 0.0 ? um : 0.0;
+        sc[1] = (!c->have_inlet || std::fabs(t[1]) < 1e-14) ? 1.0 : t[0] / t[1];
+    }
+    sc[5] = 0.0;
+    CK(cudaMemcpy(c->scal[c->cur], sc, sizeof(sc), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
 // (Re)build the tile grid and the two tile lists for tile-shape variant v.
 lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
     if (v < 0 || v >= d2q9_num_variants()) return fail(c, LBM_ERR_INVALID_ARG, "unknown tile variant");
@@ -549,9 +577,16 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
     std::vector<uint8_t> sol(N);
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) sol[(size_t)y * nx + x] = c->host_solid[(size_t)y * c->pitch + x];
+    // the current tiling's flux partials become lambda / chi values in the
+    // scalar block (valid flag 0), so a new tiling continues the same run
+    if (c->partials[c->cur] && c->scal[c->cur]) {
+        lbm_status fs = fold_partials(c);
+        if (fs != LBM_OK) return fs;
+    }
     c->variant = v;
     c->xoff = c->yoff = 0;
     c->nslots = 0;
+    c->tiling_gen += 1;
     // tile grid: keep x_{N-1} and x_N of the outlet in one tile
     d2q9_variant_tile(c->variant, &c->tx, &c->ty);
     if (c->out_face >= 0) {
@@ -617,6 +652,7 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
             for (int yy = std::max(0, y0); yy < std::min(ny, y0 + c->ty); ++yy)
                 for (int xx = std::max(0, x0); xx < std::min(nx, x0 + c->tx); ++xx)
                     own_fluid += sol[(size_t)yy * nx + xx] ? 0 : 1;
+            if (own_fluid == 0) continue;  // nothing to update: the tile is not launched
             (gen ? gen_nodes : fast_nodes_cnt) += own_fluid;
             if (gen) {
                 // face sides seen by the tile's psi halo (after the ghost mirror):
@@ -700,10 +736,362 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
     CK(cudaMemcpy(c->blocks, blist.data(), blist.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->block_flags, bflags.data(), bflags.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->block_slot, slot_all.data(), slot_all.size() * sizeof(int), cudaMemcpyHostToDevice));
-    // a new tiling renumbers the slots: the partials of the old tiling are void
+    // a new tiling renumbers the slots: old partials are void (folded above)
     CK(cudaMemset(c->scal[0] + 5, 0, sizeof(double)));
     CK(cudaMemset(c->scal[1] + 5, 0, sizeof(double)));
     return LBM_OK;
+}
+
+
+// ---- snapshots (autotuning runs trial steps and then puts the state back) ----
+struct Snapshot {
+    void* f = nullptr;
+    void* Fp = nullptr;
+    void* fo = nullptr;
+    void* rref = nullptr;
+    void* macro = nullptr;
+    double scal[8];
+    int cur = 0;
+    int64_t step = 0;
+};
+
+size_t fbytes_of(const lbm_ctx* c) { return (size_t)18 * c->plane * c->sbytes; }
+size_t nfn_of(const lbm_ctx* c) { return (size_t)std::max(1, c->nface_nodes); }
+
+lbm_status take_snapshot(lbm_ctx* c, Snapshot* s) {
+    lbm_status st = fold_partials(c);  // independent of the tiling
+    if (st != LBM_OK) return st;
+    const size_t nfn = nfn_of(c);
+    CK(cudaMalloc(&s->f, fbytes_of(c)));
+    CK(cudaMalloc(&s->Fp, nfn * 8 * c->rbytes));
+    CK(cudaMalloc(&s->fo, nfn * 18 * c->rbytes));
+    CK(cudaMalloc(&s->rref, (size_t)2 * c->plane * 2));
+    CK(cudaMalloc(&s->macro, (size_t)4 * c->plane * c->rbytes));
+    CK(cudaMemcpy(s->f, c->f[c->cur], fbytes_of(c), cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(s->Fp, c->Fp[c->cur], nfn * 8 * c->rbytes, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(s->fo, c->fo[c->cur], nfn * 18 * c->rbytes, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(s->rref, c->rref[c->cur], (size_t)2 * c->plane * 2, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(s->macro, c->macro, (size_t)4 * c->plane * c->rbytes, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(s->scal, c->scal[c->cur], sizeof(s->scal), cudaMemcpyDeviceToHost));
+    s->cur = c->cur;
+    s->step = c->step;
+    return LBM_OK;
+}
+
+lbm_status restore_snapshot(lbm_ctx* c, Snapshot* s) {
+    CK(cudaStreamSynchronize(c->stream));
+    const size_t nfn = nfn_of(c);
+    c->cur = s->cur;
+    c->step = s->step;
+    CK(cudaMemcpy(c->f[c->cur], s->f, fbytes_of(c), cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(c->Fp[c->cur], s->Fp, nfn * 8 * c->rbytes, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(c->fo[c->cur], s->fo, nfn * 18 * c->rbytes, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(c->rref[c->cur], s->rref, (size_t)2 * c->plane * 2, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(c->macro, s->macro, (size_t)4 * c->plane * c->rbytes, cudaMemcpyDeviceToDevice));
+    double sc[8];
+    std::memcpy(sc, s->scal, sizeof(sc));
+    sc[5] = 0.0;  // lambda / chi come from the folded values, whatever the tiling
+    CK(cudaMemcpy(c->scal[c->cur], sc, sizeof(sc), cudaMemcpyHostToDevice));
+    CK(cudaMemset(c->scal[1 - c->cur] + 5, 0, sizeof(double)));
+    return LBM_OK;
+}
+
+void free_snapshot(Snapshot* s) {
+    void* p[] = {s->f, s->Fp, s->fo, s->rref, s->macro};
+    for (void* q : p)
+        if (q) cudaFree(q);
+    *s = Snapshot();
+}
+
+}  // namespace
+
+// ---- batched ensembles ------------------------------------------------------
+struct lbm_batch {
+    std::vector<lbm_ctx*> m;
+    cudaStream_t stream = nullptr;
+    int precision = LBM_FP32;
+    int variant = 0;
+    int nfast = 0, ngeneral = 0;
+    int* blocks = nullptr;
+    uint8_t* flags = nullptr;
+    int* slot = nullptr;
+    unsigned* strips = nullptr;
+    int* member = nullptr;
+    void* args[4] = {nullptr, nullptr, nullptr, nullptr};  // [bpar + 2 * macros][member]
+    std::vector<int> base_cur;   // member parity when the argument arrays were built
+    std::vector<int64_t> base_gen;  // member tiling generation when they were built
+    int bpar = 0;                // steps taken since, modulo 2
+    int use_graphs = 1;
+    cudaStream_t cap_stream = nullptr, side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch* b, lbm_status st, const std::string& msg) {
+    if (b) b->err = msg;
+    else lbm::set_thread_error(msg.c_str());
+    return st;
+}
+
+#define BCK(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void free_batch_lists(lbm_batch* b) {
+    void* p[] = {b->blocks, b->flags, b->slot, b->strips, b->member, b->args[0], b->args[1], b->args[2], b->args[3]};
+    for (void* q : p)
+        if (q) cudaFree(q);
+    b->blocks = nullptr;
+    b->flags = nullptr;
+    b->slot = nullptr;
+    b->strips = nullptr;
+    b->member = nullptr;
+    for (int i = 0; i < 4; ++i) b->args[i] = nullptr;
+    for (int p2 = 0; p2 < 2; ++p2)
+        if (b->gexec[p2]) {
+            cudaGraphExecDestroy(b->gexec[p2]);
+            b->gexec[p2] = nullptr;
+        }
+}
+
+// Concatenate the members' tile lists (fast tiles first, then general tiles)
+// and upload the per-member argument blocks for both parities.
+template <typename S, typename R>
+lbm_status build_batch(lbm_batch* b) {
+    // one kernel instantiation serves the whole batch: every member must use
+    // the tile shape of the first one (members re-tiled on their own follow)
+    const int v = b->m[0]->variant;
+    for (lbm_ctx* c : b->m)
+        if (c->variant != v) {
+            lbm_status st = build_tiles(c, v, true);
+            if (st != LBM_OK) return bfail(b, st, c->err);
+        }
+    b->variant = v;
+    free_batch_lists(b);
+    b->nfast = 0;
+    b->ngeneral = 0;
+    std::vector<int> blk, mem, slt;
+    std::vector<uint8_t> flg;
+    std::vector<unsigned> stp;
+    for (int pass = 0; pass < 2; ++pass)
+        for (size_t mi = 0; mi < b->m.size(); ++mi) {
+            lbm_ctx* c = b->m[mi];
+            const int n = pass == 0 ? c->nfast : c->ngeneral;
+            const int off = pass == 0 ? 0 : c->nfast;
+            if (n == 0) continue;
+            std::vector<int> cb(n), cs(n);
+            std::vector<uint8_t> cf(n);
+            std::vector<unsigned> cst(n);
+            BCK(cudaMemcpy(cb.data(), c->blocks + off, n * sizeof(int), cudaMemcpyDeviceToHost));
+            BCK(cudaMemcpy(cf.data(), c->block_flags + off, n, cudaMemcpyDeviceToHost));
+            BCK(cudaMemcpy(cs.data(), c->block_slot + off, n * sizeof(int), cudaMemcpyDeviceToHost));
+            BCK(cudaMemcpy(cst.data(), c->block_strips + off, n * sizeof(unsigned), cudaMemcpyDeviceToHost));
+            blk.insert(blk.end(), cb.begin(), cb.end());
+            flg.insert(flg.end(), cf.begin(), cf.end());
+            slt.insert(slt.end(), cs.begin(), cs.end());
+            stp.insert(stp.end(), cst.begin(), cst.end());
+            mem.insert(mem.end(), (size_t)n, (int)mi);
+            (pass == 0 ? b->nfast : b->ngeneral) += n;
+        }
+    if ((size_t)b->nfast + (size_t)b->ngeneral != blk.size() || mem.size() != blk.size())
+        return bfail(b, LBM_ERR_INVALID_ARG, "inconsistent batch tile lists");
+    const size_t nt = blk.size() + 1;
+    BCK(cudaMalloc((void**)&b->blocks, nt * sizeof(int)));
+    BCK(cudaMalloc((void**)&b->flags, nt));
+    BCK(cudaMalloc((void**)&b->slot, nt * sizeof(int)));
+    BCK(cudaMalloc((void**)&b->strips, nt * sizeof(unsigned)));
+    BCK(cudaMalloc((void**)&b->member, nt * sizeof(int)));
+    BCK(cudaMemcpy(b->blocks, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->flags, flg.data(), flg.size(), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->slot, slt.data(), slt.size() * sizeof(int), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->strips, stp.data(), stp.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->member, mem.data(), mem.size() * sizeof(int), cudaMemcpyHostToDevice));
+    b->base_cur.resize(b->m.size());
+    b->base_gen.resize(b->m.size());
+    for (size_t mi = 0; mi < b->m.size(); ++mi) b->base_gen[mi] = b->m[mi]->tiling_gen;
+    for (int q = 0; q < 4; ++q) {
+        std::vector<D2Args<S, R>> av(b->m.size());
+        for (size_t mi = 0; mi < b->m.size(); ++mi) {
+            b->base_cur[mi] = b->m[mi]->cur;
+            av[mi] = make_args_par<S, R>(b->m[mi], b->m[mi]->cur ^ (q & 1), q >= 2);
+        }
+        BCK(cudaMalloc(&b->args[q], av.size() * sizeof(D2Args<S, R>)));
+        BCK(cudaMemcpy(b->args[q], av.data(), av.size() * sizeof(D2Args<S, R>), cudaMemcpyHostToDevice));
+    }
+    b->bpar = 0;
+    return LBM_OK;
+}
+
+template <typename S, typename R>
+cudaError_t batch_launch(lbm_batch* b, bool macros, cudaStream_t st, cudaStream_t side) {
+    BatchArgs<S, R> a{};
+    a.args = static_cast<const D2Args<S, R>*>(b->args[b->bpar + (macros ? 2 : 0)]);
+    a.blocks = b->blocks;
+    a.flags = b->flags;
+    a.slot = b->slot;
+    a.strips = b->strips;
+    a.member = b->member;
+    a.off = 0;
+    cudaError_t e = cudaSuccess;
+    const bool fork = side && b->nfast > 0 && b->ngeneral > 0;
+    if (fork) {
+        e = cudaEventRecord(b->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, b->ev_fork, 0);
+    }
+    if (e == cudaSuccess) e = launch_d2q9_batch<S, R>(a, b->variant, false, b->nfast, st);
+    a.off = b->nfast;
+    if (e == cudaSuccess) e = launch_d2q9_batch<S, R>(a, b->variant, true, b->ngeneral, fork ? side : st);
+    if (fork && e == cudaSuccess) {
+        e = cudaEventRecord(b->ev_join, side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->ev_join, 0);
+    }
+    return e;
+}
+
+void batch_advance(lbm_batch* b, int64_t n) {
+    for (lbm_ctx* c : b->m) {
+        if (n & 1) c->cur = 1 - c->cur;
+        c->step += n;
+    }
+    if (n & 1) b->bpar ^= 1;
+    b->launches += n * ((b->nfast > 0) + (b->ngeneral > 0));
+}
+
+template <typename S, typename R>
+lbm_status batch_graph(lbm_batch* b, int par) {
+    if (b->gexec[par]) return LBM_OK;
+    if (!b->cap_stream) BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    if (!b->side_stream) BCK(cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking));
+    if (!b->ev_fork) BCK(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    if (!b->ev_join) BCK(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+    const int saved = b->bpar;
+    b->bpar = par;
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kGraphSteps && e == cudaSuccess; ++i) {
+        e = batch_launch<S, R>(b, false, b->cap_stream, b->side_stream);
+        b->bpar ^= 1;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+    b->bpar = saved;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec[par], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->gexec[par] = nullptr;
+        return bfail(b, LBM_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+template <typename S, typename R>
+lbm_status batch_run(lbm_batch* b, int64_t n) {
+    // a member stepped or re-tiled on its own since the arrays were built:
+    // rebuild them (its buffers or parity changed)
+    for (size_t mi = 0; mi < b->m.size(); ++mi)
+        if ((b->m[mi]->cur ^ b->base_cur[mi]) != b->bpar || b->m[mi]->tiling_gen != b->base_gen[mi]) {
+            BCK(cudaStreamSynchronize(b->stream));
+            lbm_status st = build_batch<S, R>(b);
+            if (st != LBM_OK) return st;
+            break;
+        }
+    int64_t rem = n;
+    while (rem > 1) {
+        if (b->use_graphs && rem - 1 >= kGraphSteps) {
+            if (batch_graph<S, R>(b, b->bpar) != LBM_OK) {
+                b->use_graphs = 0;
+                cudaGetLastError();
+                continue;
+            }
+            BCK(cudaGraphLaunch(b->gexec[b->bpar], b->stream));
+            batch_advance(b, kGraphSteps);  // even: bpar unchanged
+            rem -= kGraphSteps;
+            continue;
+        }
+        BCK((batch_launch<S, R>(b, false, b->stream, nullptr)));
+        batch_advance(b, 1);
+        --rem;
+    }
+    if (rem == 1) {
+        BCK((batch_launch<S, R>(b, true, b->stream, nullptr)));
+        batch_advance(b, 1);
+    }
+    return LBM_OK;
+}
+
+template <typename S, typename R>
+lbm_status batch_dispatch_build(lbm_batch* b) { return build_batch<S, R>(b); }
+
+lbm_status batch_build_any(lbm_batch* b) {
+    if (b->precision == LBM_FP64) return batch_dispatch_build<double, double>(b);
+    if (b->precision == LBM_FP32) return batch_dispatch_build<float, float>(b);
+    return batch_dispatch_build<__half, float>(b);
+}
+
+lbm_status batch_run_any(lbm_batch* b, int64_t n) {
+    if (b->precision == LBM_FP64) return batch_run<double, double>(b, n);
+    if (b->precision == LBM_FP32) return batch_run<float, float>(b, n);
+    return batch_run<__half, float>(b, n);
+}
+
+// Time `steps` steps of every tile variant from the same starting state and
+// keep the fastest (members' states are restored afterwards).
+lbm_status batch_autotune(lbm_batch* b, int steps, int* chosen, double* best_ms) {
+    BCK(cudaStreamSynchronize(b->stream));
+    std::vector<Snapshot> snaps(b->m.size());
+    for (size_t i = 0; i < b->m.size(); ++i) {
+        lbm_status st = take_snapshot(b->m[i], &snaps[i]);
+        if (st != LBM_OK) return bfail(b, st, b->m[i]->err);
+    }
+    cudaEvent_t t0, t1;
+    BCK(cudaEventCreate(&t0));
+    BCK(cudaEventCreate(&t1));
+    int best = -1;
+    double bestms = 1e300;
+    lbm_status st = LBM_OK;
+    for (int v = 0; v < d2q9_num_variants() && st == LBM_OK; ++v) {
+        for (size_t i = 0; i < b->m.size() && st == LBM_OK; ++i) {
+            st = restore_snapshot(b->m[i], &snaps[i]);
+            if (st == LBM_OK) st = build_tiles(b->m[i], v, true);
+        }
+        if (st != LBM_OK) break;
+        b->variant = v;
+        st = batch_build_any(b);
+        if (st != LBM_OK) break;
+        st = batch_run_any(b, std::max(2, steps / 4));  // warm-up (also captures the graphs)
+        if (st != LBM_OK) break;
+        BCK(cudaEventRecord(t0, b->stream));
+        st = batch_run_any(b, steps);
+        BCK(cudaEventRecord(t1, b->stream));
+        BCK(cudaEventSynchronize(t1));
+        float ms = 0.0f;
+        BCK(cudaEventElapsedTime(&ms, t0, t1));
+        if (ms < bestms) {
+            bestms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    for (size_t i = 0; i < b->m.size(); ++i) {
+        lbm_status s2 = restore_snapshot(b->m[i], &snaps[i]);
+        if (s2 == LBM_OK && best >= 0) s2 = build_tiles(b->m[i], best, true);
+        free_snapshot(&snaps[i]);
+        if (st == LBM_OK) st = s2;
+    }
+    if (st != LBM_OK) return st;
+    b->variant = best;
+    st = batch_build_any(b);
+    *chosen = best;
+    if (best_ms) *best_ms = bestms / steps;
+    return st;
 }
 
 }  // namespace
@@ -1199,6 +1587,113 @@ lbm_status lbm_set_graph_mode(lbm_ctx* c, int use_graphs) {
     c->use_graphs = use_graphs ? 1 : 0;
     return LBM_OK;
 }
+
+lbm_status lbm_batch_create(lbm_ctx* const* members, int n, void* cuda_stream, lbm_batch** out) {
+    if (!out) return bfail(nullptr, LBM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!members || n < 1) return bfail(nullptr, LBM_ERR_INVALID_ARG, "need at least one member");
+    for (int i = 0; i < n; ++i) {
+        if (!members[i]) return bfail(nullptr, LBM_ERR_INVALID_ARG, "NULL member");
+        if (members[i]->precision != members[0]->precision)
+            return bfail(nullptr, LBM_ERR_INVALID_ARG, "members must share one precision");
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return bfail(nullptr, LBM_ERR_INVALID_ARG, "a member appears twice");
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return bfail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    b->m.assign(members, members + n);
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->precision = members[0]->precision;
+    b->variant = members[0]->variant;
+    lbm_status st = LBM_OK;
+    for (lbm_ctx* c : b->m)
+        if (st == LBM_OK && c->variant != b->variant) st = build_tiles(c, b->variant, true);
+    if (st == LBM_OK) st = batch_build_any(b);
+    if (st != LBM_OK) {
+        const std::string msg = b->err;
+        free_batch_lists(b);
+        delete b;
+        return bfail(nullptr, st, msg);
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "batch is NULL");
+    if (nsteps < 0) return bfail(b, LBM_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if (nsteps == 0) return LBM_OK;
+    return batch_run_any(b, nsteps);
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b) {
+    if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "batch is NULL");
+    BCK(cudaStreamSynchronize(b->stream));
+    for (lbm_ctx* c : b->m) {
+        lbm_status st = check_status(c);
+        if (st != LBM_OK) return bfail(b, st, c->err);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_tile_variant(lbm_batch* b, int variant) {
+    if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "batch is NULL");
+    if (variant < 0 || variant >= d2q9_num_variants()) return bfail(b, LBM_ERR_INVALID_ARG, "unknown tile variant");
+    BCK(cudaStreamSynchronize(b->stream));
+    for (lbm_ctx* c : b->m) BCK(cudaStreamSynchronize(c->stream));
+    for (lbm_ctx* c : b->m) {
+        lbm_status st = build_tiles(c, variant, true);
+        if (st != LBM_OK) return bfail(b, st, c->err);
+    }
+    b->variant = variant;
+    return batch_build_any(b);
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int steps, int* variant, double* ms_per_step) {
+    if (!b || !variant || steps < 1) return bfail(b, LBM_ERR_INVALID_ARG, "bad autotune request");
+    return batch_autotune(b, steps, variant, ms_per_step);
+}
+
+lbm_status lbm_autotune(lbm_ctx* c, int steps, int* variant, double* ms_per_step) {
+    if (!c || !variant || steps < 1) return fail(c, LBM_ERR_INVALID_ARG, "bad autotune request");
+    lbm_batch* b = nullptr;
+    lbm_ctx* one[1] = {c};
+    lbm_status st = lbm_batch_create(one, 1, c->stream, &b);
+    if (st != LBM_OK) return fail(c, st, lbm_last_error(nullptr));
+    st = batch_autotune(b, steps, variant, ms_per_step);
+    if (st != LBM_OK) fail(c, st, b->err);
+    lbm_batch_destroy(b);
+    return st;
+}
+
+lbm_status lbm_batch_info(lbm_batch* b, int* variant, int* fast_tiles, int* general_tiles, int64_t* launches) {
+    if (!b || !variant || !fast_tiles || !general_tiles || !launches)
+        return bfail(b, LBM_ERR_INVALID_ARG, "NULL argument");
+    *variant = b->variant;
+    *fast_tiles = b->nfast;
+    *general_tiles = b->ngeneral;
+    *launches = b->launches;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_graph_mode(lbm_batch* b, int use_graphs) {
+    if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "batch is NULL");
+    b->use_graphs = use_graphs ? 1 : 0;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    free_batch_lists(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->side_stream) cudaStreamDestroy(b->side_stream);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    delete b;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : lbm_last_error(nullptr); }
 
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;

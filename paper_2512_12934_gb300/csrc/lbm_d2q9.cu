@@ -594,8 +594,11 @@ __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSm
     }
 }
 
+// One tile of one step.  bxy = bx | by << 16; bflags = BLOCK_* flags; strips
+// and slot are used by general tiles only.
 template <typename S, typename R, int TX, int TY, bool GEN>
-__global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
+__device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsigned bflags, unsigned strips,
+                                          int slot) {
     constexpr int NT = TX * TY, NW = NT / 32;
     using SmemT = typename std::conditional<GEN, TileSmemGen<S, R, TX, TY>, TileSmem<S, R, TX, TY>>::type;
     __shared__ SmemT smx;
@@ -603,9 +606,6 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int li = a.list_off + blockIdx.x;
-    const int bxy = a.blocks[li];
-    const unsigned bflags = a.block_flags[li];
     const int x0 = (bxy & 0xffff) * TX - a.xoff, y0 = (bxy >> 16) * TY - a.yoff;
     const int x = x0 + tx, y = y0 + ty;
 
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
     unsigned info;
     bool fluid;
     if constexpr (GEN)
-        stage_tile_general<S, R, TX, TY>(a, smx, x0, y0, tx, ty, a.block_strips[li], bflags, f, info, fluid);
+        stage_tile_general<S, R, TX, TY>(a, smx, x0, y0, tx, ty, strips, bflags, f, info, fluid);
     else if (bflags & BLOCK_EDGE) stage_tile<S, R, TX, TY, 1>(a, sm, x0, y0, tx, ty, f, info, fluid);
     else stage_tile<S, R, TX, TY, 0>(a, sm, x0, y0, tx, ty, f, info, fluid);
     __syncthreads();
@@ -790,7 +790,6 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
 
     // ---- FP64 flux reductions for lambda (Eq. 21) and chi (Eq. 23) ----
     if (GEN && a.nslots > 0) {
-        const int slot = a.block_slot[li];
         if (slot >= 0) {
             double v[4] = {0.0, 0.0, 0.0, 0.0};
             if (fluid && own_face >= 0 && a.face[own_face].kind == FACE_INLET) {
@@ -823,6 +822,32 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
             }
         }
     }
+}
+
+// Single-instance step: one tile of the launch's list per CTA.
+template <typename S, typename R, int TX, int TY, bool GEN>
+__global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
+    const int li = a.list_off + blockIdx.x;
+    step_tile<S, R, TX, TY, GEN>(a, a.blocks[li], a.block_flags[li], GEN ? a.block_strips[li] : 0u,
+                                 GEN ? a.block_slot[li] : -1);
+}
+
+// Batched step: the list interleaves the tiles of many instances; each CTA
+// copies its instance's arguments into shared memory and runs the same tile
+// code, so a batch step equals stepping every member on its own.
+template <typename S, typename R, int TX, int TY, bool GEN>
+__global__ void __launch_bounds__(TX * TY) d2q9_batch_kernel(const __grid_constant__ BatchArgs<S, R> b) {
+    __shared__ D2Args<S, R> sa;
+    const int li = b.off + blockIdx.x;
+    const int m = b.member[li];
+    {
+        static_assert(sizeof(D2Args<S, R>) % 4 == 0, "argument block must be word-sized");
+        const int* src = reinterpret_cast<const int*>(b.args + m);
+        int* dst = reinterpret_cast<int*>(&sa);
+        for (int i = threadIdx.x; i < (int)(sizeof(D2Args<S, R>) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    step_tile<S, R, TX, TY, GEN>(sa, b.blocks[li], b.flags[li], b.strips[li], b.slot[li]);
 }
 
 // FP64 mass / speed reduction for diagnostics.
@@ -909,6 +934,25 @@ static void launch_tile(const D2Args<S, R>& a, bool general, int nblocks, cudaSt
     else d2q9_step_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(a);
 }
 
+template <typename S, typename R, int TX, int TY>
+static void launch_batch_tile(const BatchArgs<S, R>& b, bool general, int nblocks, cudaStream_t st) {
+    if (general) d2q9_batch_kernel<S, R, TX, TY, true><<<nblocks, TX * TY, 0, st>>>(b);
+    else d2q9_batch_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(b);
+}
+
+template <typename S, typename R>
+cudaError_t launch_d2q9_batch(const BatchArgs<S, R>& b, int variant, bool general, int nblocks, cudaStream_t st) {
+    if (nblocks <= 0) return cudaSuccess;
+    switch (variant) {
+    case 0: launch_batch_tile<S, R, 32, 8>(b, general, nblocks, st); break;
+    case 1: launch_batch_tile<S, R, 32, 4>(b, general, nblocks, st); break;
+    case 2: launch_batch_tile<S, R, 64, 4>(b, general, nblocks, st); break;
+    case 3: launch_batch_tile<S, R, 32, 16>(b, general, nblocks, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <typename S, typename R>
 cudaError_t launch_d2q9_step(const D2Args<S, R>& a, int variant, bool general, int nblocks, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
@@ -930,6 +974,9 @@ cudaError_t launch_d2q9_diag(const S* f, const R* macro, const uint16_t* info, c
     return cudaGetLastError();
 }
 
+template cudaError_t launch_d2q9_batch<float, float>(const BatchArgs<float, float>&, int, bool, int, cudaStream_t);
+template cudaError_t launch_d2q9_batch<double, double>(const BatchArgs<double, double>&, int, bool, int, cudaStream_t);
+template cudaError_t launch_d2q9_batch<__half, float>(const BatchArgs<__half, float>&, int, bool, int, cudaStream_t);
 template cudaError_t launch_d2q9_step<float, float>(const D2Args<float, float>&, int, bool, int, cudaStream_t);
 template cudaError_t launch_d2q9_step<double, double>(const D2Args<double, double>&, int, bool, int, cudaStream_t);
 template cudaError_t launch_d2q9_step<__half, float>(const D2Args<__half, float>&, int, bool, int, cudaStream_t);

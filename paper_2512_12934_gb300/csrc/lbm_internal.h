@@ -87,6 +87,22 @@ struct D2Args {
     R body[2];
 };
 
+// Batched step: tile list entries of many instances; member[] names the
+// instance whose arguments (args[member]) a tile uses.
+template <typename S, typename R>
+struct BatchArgs {
+    const D2Args<S, R>* args;
+    const int* blocks;
+    const uint8_t* flags;
+    const int* slot;
+    const unsigned* strips;
+    const int* member;
+    int off;
+};
+
+template <typename S, typename R>
+cudaError_t launch_d2q9_batch(const BatchArgs<S, R>& b, int variant, bool general, int nblocks, cudaStream_t st);
+
 // Launch one list of tiles of one step: general = false -> fast kernel,
 // true -> general kernel; nblocks list entries starting at a.list_off.
 template <typename S, typename R>

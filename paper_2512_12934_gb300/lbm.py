@@ -115,6 +115,26 @@ def load():
     L.lbm_mass_noalloc.restype = ctypes.c_int
     L.lbm_mass_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.lbm_batch_create.restype = ctypes.c_int
+    L.lbm_batch_create.argtypes = [ctypes.POINTER(c_ctx), ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(c_ctx)]
+    L.lbm_batch_step.restype = ctypes.c_int
+    L.lbm_batch_step.argtypes = [c_ctx, ctypes.c_int64]
+    L.lbm_batch_sync.restype = ctypes.c_int
+    L.lbm_batch_sync.argtypes = [c_ctx]
+    L.lbm_batch_set_tile_variant.restype = ctypes.c_int
+    L.lbm_batch_set_tile_variant.argtypes = [c_ctx, ctypes.c_int]
+    L.lbm_batch_autotune.restype = ctypes.c_int
+    L.lbm_batch_autotune.argtypes = [c_ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    L.lbm_autotune.restype = ctypes.c_int
+    L.lbm_autotune.argtypes = [c_ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    L.lbm_batch_info.restype = ctypes.c_int
+    L.lbm_batch_info.argtypes = [c_ctx] + [ctypes.POINTER(ctypes.c_int)] * 3 + [ctypes.POINTER(ctypes.c_int64)]
+    L.lbm_batch_set_graph_mode.restype = ctypes.c_int
+    L.lbm_batch_set_graph_mode.argtypes = [c_ctx, ctypes.c_int]
+    L.lbm_batch_destroy.restype = None
+    L.lbm_batch_destroy.argtypes = [c_ctx]
+    L.lbm_batch_last_error.restype = ctypes.c_char_p
+    L.lbm_batch_last_error.argtypes = [c_ctx]
     L.lbm_version.restype = ctypes.c_char_p
     L.lbm_version.argtypes = []
     _lib = L
@@ -269,11 +289,73 @@ class Solver:
     def set_graph_mode(self, on):
         _check(load().lbm_set_graph_mode(self.h, int(bool(on))), self.h)
 
+    def autotune(self, steps=20):
+        v = ctypes.c_int()
+        ms = ctypes.c_double()
+        _check(load().lbm_autotune(self.h, int(steps), ctypes.byref(v), ctypes.byref(ms)), self.h)
+        return v.value, ms.value
+
     def save(self, path):
         _check(load().lbm_save(self.h, path.encode()), self.h)
 
     def load_checkpoint(self, path):
         _check(load().lbm_load(self.h, path.encode()), self.h)
+
+
+class Batch:
+    """A batched ensemble over existing Solver objects (lbm_batch_*)."""
+
+    def __init__(self, members, stream=None):
+        L = load()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m.h.value for m in self.members])
+        h = ctypes.c_void_p()
+        st = L.lbm_batch_create(ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), len(self.members),
+                                ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if st != LBM_OK:
+            msg = L.lbm_batch_last_error(None)
+            raise LbmError(st, msg.decode() if msg else "")
+        self.h = h
+
+    def _check(self, st):
+        if st != LBM_OK:
+            msg = load().lbm_batch_last_error(self.h)
+            raise LbmError(st, msg.decode() if msg else "")
+
+    def step(self, n=1):
+        self._check(load().lbm_batch_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(load().lbm_batch_sync(self.h))
+
+    def set_tile_variant(self, v):
+        self._check(load().lbm_batch_set_tile_variant(self.h, int(v)))
+
+    def autotune(self, steps=20):
+        v = ctypes.c_int()
+        ms = ctypes.c_double()
+        self._check(load().lbm_batch_autotune(self.h, int(steps), ctypes.byref(v), ctypes.byref(ms)))
+        return v.value, ms.value
+
+    def info(self):
+        v, a, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        n = ctypes.c_int64()
+        self._check(load().lbm_batch_info(self.h, ctypes.byref(v), ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+        return {"variant": v.value, "fast_tiles": a.value, "general_tiles": b.value, "launches": n.value}
+
+    def set_graph_mode(self, on):
+        self._check(load().lbm_batch_set_graph_mode(self.h, int(bool(on))))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mass_noalloc(f_ptr, precision, nx, ny, pitch, solid_ptr, mass_ptr, stream=None):

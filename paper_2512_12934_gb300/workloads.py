@@ -211,3 +211,28 @@ def tjunction(Wc=40, length_factor=20, Wd=None, side_len=None, x_side=None, Ca=0
     u[:, solid != 0] = 0.0
     return Workload("tjunction_Wc%d" % Wc, cfg, solid, rho, u, 0,
                     {"Wc": Wc, "Wd": Wd, "x_side": x_side, "Ca": Ca, "q_ratio": q_ratio, "M": M})
+
+
+def tjunction_ensemble(n=256, seed=2512004, wc_range=(40, 120), G12=2.0, Gw=(0.2, -0.2), gamma=0.25,
+                       u_cap=0.05, length_factor=20):
+    """Seeded ensemble of T-junction droplet generators with uneven sizes and
+    parameters: W_c ~ U{wc_range}, W_d = U(0.5, 1) W_c, main channel length
+    length_factor * W_c, side channel 2 W_c, Ca ~ logU[0.002, 0.05],
+    Q_d/Q_c ~ logU[0.2, 5], M = nu_d/nu_c ~ logU[0.1, 10].  The continuous
+    inflow speed follows Ca = u_c nu_c rho / gamma with nu_c = 1/6, rho = 1 and
+    the given surface tension gamma (lattice units), capped at u_cap."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(n):
+        Wc = int(rng.integers(wc_range[0], wc_range[1] + 1))
+        Wd = max(4, int(round(rng.uniform(0.5, 1.0) * Wc)))
+        Ca = float(np.exp(rng.uniform(np.log(0.002), np.log(0.05))))
+        q = float(np.exp(rng.uniform(np.log(0.2), np.log(5.0))))
+        M = float(np.exp(rng.uniform(np.log(0.1), np.log(10.0))))
+        nu_c = 1.0 / 6.0
+        u_c = min(u_cap, Ca * gamma / nu_c)
+        w = tjunction(Wc=Wc, length_factor=length_factor, Wd=Wd, side_len=2 * Wc, x_side=4 * Wc, Ca=Ca,
+                      q_ratio=q, M=M, G12=G12, Gw=Gw, u_c=u_c, nu_c=nu_c, seed=seed + j)
+        w.name = "tjunction_%03d" % j
+        out.append(w)
+    return out
