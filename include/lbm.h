@@ -292,6 +292,62 @@ void lbm_batch_destroy(lbm_batch* b);
 /* Message of the batch's last failure (b == NULL: the thread's last). */
 const char* lbm_batch_last_error(const lbm_batch* b);
 
+/* ---- Surrogate MLP ensemble ---------------------------------------------
+ * The paper has no counterpart: it reports droplet sizes and generation
+ * periods of T-junction and co-flow devices as functions of Ca, the flow-rate
+ * ratio, the viscosity ratio and the width ratio (Sec. 4, Figs. 10-11); the
+ * surrogate learns that map from runs of this solver.
+ * Network of one member: x (4) -> 128 -> 128 -> 128 -> y (2), GELU
+ * (z * Phi(z), the erf form) after each hidden layer, FP32 throughout.
+ * Loss: mean squared error over the batch and both outputs.  Optimiser: Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).
+ * Parameters of one member, flat float order (row-major, output index
+ * first): W1[128][4], b1[128], W2[128][128], b2[128], W3[128][128], b3[128],
+ * W4[2][128], b4[2]; lbm_mlp_num_params() floats.  All members lie back to
+ * back: [members][num_params].
+ * Host arrays: X [n][4] inputs, T [n][2] targets, row-major.  Every call
+ * waits for its own work; device scratch is allocated per call.  One
+ * lbm_mlp is not thread-safe. */
+typedef struct lbm_mlp lbm_mlp;
+
+int64_t lbm_mlp_num_params(void);
+
+/* members in [1, 64]; weights uniform in +-1/sqrt(fan_in) from a splitmix64
+ * stream seeded per member, biases 0; Adam moments 0. */
+lbm_status lbm_mlp_create(int members, uint64_t seed, void* cuda_stream, lbm_mlp** out);
+
+/* Replace all members' parameters (host, members*num_params floats); resets
+ * the Adam moments and step count. */
+lbm_status lbm_mlp_set_params(lbm_mlp* m, const float* params);
+/* Copy all members' parameters out (host, members*num_params floats). */
+lbm_status lbm_mlp_get_params(lbm_mlp* m, float* params);
+
+/* Every member's output on n inputs: Y [members][n][2] (host). */
+lbm_status lbm_mlp_forward(lbm_mlp* m, const float* X, int n, float* Y);
+
+/* Full-batch gradient of every member's loss on (X, T): grad
+ * [members][num_params] (host).  Parameters are not changed. */
+lbm_status lbm_mlp_gradient(lbm_mlp* m, const float* X, const float* T, int n, float* grad);
+
+/* Adam training: `epochs` passes over (X, T), each a splitmix64
+ * Fisher-Yates shuffle (seeded by shuffle_seed, continued across epochs)
+ * cut into minibatches of `batch` rows (a ragged tail is dropped); every
+ * member sees the same minibatches.  batch > n is clamped to n. */
+lbm_status lbm_mlp_train(lbm_mlp* m, const float* X, const float* T, int n, int epochs, int batch, double lr,
+                         uint64_t shuffle_seed);
+
+/* Ensemble prediction on n inputs: mean [n][2] and spread [n], the largest
+ * over the two outputs of (population std over members) / |mean|.
+ * dst_is_device != 0: X, mean and spread are device pointers on the
+ * library's device (enqueued on the stream, still waited for). */
+lbm_status lbm_mlp_predict(lbm_mlp* m, const float* X, int n, float* mean, float* spread, int dst_is_device);
+
+/* Release the ensemble.  NULL is ignored. */
+void lbm_mlp_destroy(lbm_mlp* m);
+
+/* Message of the ensemble's last failure (m == NULL: the thread's last). */
+const char* lbm_mlp_last_error(const lbm_mlp* m);
+
 /* Release all device memory of the context.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);
 

@@ -137,6 +137,28 @@ def load():
     L.lbm_batch_last_error.argtypes = [c_ctx]
     L.lbm_version.restype = ctypes.c_char_p
     L.lbm_version.argtypes = []
+    c_mlp = ctypes.c_void_p
+    L.lbm_mlp_num_params.restype = ctypes.c_int64
+    L.lbm_mlp_num_params.argtypes = []
+    L.lbm_mlp_create.restype = ctypes.c_int
+    L.lbm_mlp_create.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(c_mlp)]
+    L.lbm_mlp_set_params.restype = ctypes.c_int
+    L.lbm_mlp_set_params.argtypes = [c_mlp, _fp]
+    L.lbm_mlp_get_params.restype = ctypes.c_int
+    L.lbm_mlp_get_params.argtypes = [c_mlp, _fp]
+    L.lbm_mlp_forward.restype = ctypes.c_int
+    L.lbm_mlp_forward.argtypes = [c_mlp, _fp, ctypes.c_int, _fp]
+    L.lbm_mlp_gradient.restype = ctypes.c_int
+    L.lbm_mlp_gradient.argtypes = [c_mlp, _fp, _fp, ctypes.c_int, _fp]
+    L.lbm_mlp_train.restype = ctypes.c_int
+    L.lbm_mlp_train.argtypes = [c_mlp, _fp, _fp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_uint64]
+    L.lbm_mlp_predict.restype = ctypes.c_int
+    L.lbm_mlp_predict.argtypes = [c_mlp, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    L.lbm_mlp_destroy.restype = None
+    L.lbm_mlp_destroy.argtypes = [c_mlp]
+    L.lbm_mlp_last_error.restype = ctypes.c_char_p
+    L.lbm_mlp_last_error.argtypes = [c_mlp]
     _lib = L
     return L
 
@@ -365,6 +387,89 @@ def mass_noalloc(f_ptr, precision, nx, ny, pitch, solid_ptr, mass_ptr, stream=No
     _check(load().lbm_mass_noalloc(ctypes.c_void_p(f_ptr), p, int(nx), int(ny), int(pitch),
                                    ctypes.c_void_p(solid_ptr or 0), ctypes.c_void_p(mass_ptr),
                                    ctypes.c_void_p(stream or 0)), None)
+
+
+class MLP:
+    """Surrogate MLP ensemble (lbm_mlp_*): members of 4 -> 128 -> 128 ->
+    128 -> 2 with GELU, trained and evaluated by the library's kernels."""
+
+    def __init__(self, members=5, seed=0, stream=None):
+        L = load()
+        h = ctypes.c_void_p()
+        st = L.lbm_mlp_create(int(members), int(seed), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if st != LBM_OK:
+            msg = L.lbm_mlp_last_error(None)
+            raise LbmError(st, msg.decode() if msg else "")
+        self.h = h
+        self.members = int(members)
+        self.P = int(L.lbm_mlp_num_params())
+
+    def _check(self, st):
+        if st != LBM_OK:
+            msg = load().lbm_mlp_last_error(self.h)
+            raise LbmError(st, msg.decode() if msg else "")
+
+    @staticmethod
+    def _f32(a, cols):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        if a.ndim != 2 or a.shape[1] != cols:
+            raise ValueError("expected an [n][%d] array, got %s" % (cols, a.shape))
+        return a
+
+    def set_params(self, flat):
+        """flat: [members][P] (or members*P) floats; resets Adam."""
+        a = np.ascontiguousarray(flat, dtype=np.float32).reshape(-1)
+        if a.size != self.members * self.P:
+            raise ValueError("expected %d parameters" % (self.members * self.P))
+        self._check(load().lbm_mlp_set_params(self.h, a.ctypes.data_as(_fp)))
+
+    def params(self):
+        out = np.zeros(self.members * self.P, dtype=np.float32)
+        self._check(load().lbm_mlp_get_params(self.h, out.ctypes.data_as(_fp)))
+        return out.reshape(self.members, self.P)
+
+    def forward(self, X):
+        X = self._f32(X, 4)
+        Y = np.zeros((self.members, X.shape[0], 2), dtype=np.float32)
+        self._check(load().lbm_mlp_forward(self.h, X.ctypes.data_as(_fp), X.shape[0], Y.ctypes.data_as(_fp)))
+        return Y
+
+    def gradient(self, X, T):
+        X, T = self._f32(X, 4), self._f32(T, 2)
+        g = np.zeros((self.members, self.P), dtype=np.float32)
+        self._check(load().lbm_mlp_gradient(self.h, X.ctypes.data_as(_fp), T.ctypes.data_as(_fp), X.shape[0],
+                                            g.ctypes.data_as(_fp)))
+        return g
+
+    def train(self, X, T, epochs, batch=256, lr=1e-3, shuffle_seed=0):
+        X, T = self._f32(X, 4), self._f32(T, 2)
+        self._check(load().lbm_mlp_train(self.h, X.ctypes.data_as(_fp), T.ctypes.data_as(_fp), X.shape[0],
+                                         int(epochs), int(batch), float(lr), int(shuffle_seed)))
+
+    def predict(self, X):
+        """Ensemble mean [n][2] and relative spread [n] (host arrays)."""
+        X = self._f32(X, 4)
+        n = X.shape[0]
+        mean = np.zeros((n, 2), dtype=np.float32)
+        spread = np.zeros(n, dtype=np.float32)
+        self._check(load().lbm_mlp_predict(self.h, X.ctypes.data, n, mean.ctypes.data, spread.ctypes.data, 0))
+        return mean, spread
+
+    def predict_device(self, x_ptr, n, mean_ptr, spread_ptr):
+        """Device-pointer form: X [n][4], mean [n][2], spread [n] (float32)."""
+        self._check(load().lbm_mlp_predict(self.h, ctypes.c_void_p(x_ptr), int(n), ctypes.c_void_p(mean_ptr),
+                                           ctypes.c_void_p(spread_ptr), 1))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version():

@@ -101,3 +101,12 @@ def test_unsupported_lattice_reported(L):
                       rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, None, ctypes.byref(h))
     assert st == 6 and not h.value
     assert L.lbm_last_error(None)
+
+
+def test_mlp_parameter_count_and_argument_checks(L):
+    from oracle import mlp_oracle as M
+    assert L.lbm_mlp_num_params() == M.n_params()
+    for members in (0, -1, 65):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.MLP(members)
+        assert e.value.status == 1
