@@ -41,7 +41,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--lbm-steps", type=int, default=5000, help="LBM time steps per benchmark step")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16store", "fp64"])
-    p.add_argument("--workload", default="channel", choices=["channel", "channel_hbm", "tjunction_batch"],
+    p.add_argument("--workload", default="channel",
+                   choices=["channel", "channel_hbm", "tjunction_batch", "surrogate"],
                    help="channel: the 1024x128 config; channel_hbm: the same physics on 8192x2048; "
                         "tjunction_batch: the T-junction ensemble, batched vs sequential")
     p.add_argument("--instances", type=int, default=256, help="ensemble size for tjunction_batch")
@@ -50,6 +51,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-hbm", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--sur-train", type=int, default=1024, help="solver runs used to train the surrogate")
+    p.add_argument("--sur-test", type=int, default=256, help="held-out solver runs judging the surrogate")
+    p.add_argument("--no-mlp", action="store_true", help="skip the surrogate-kernel entry of the default line")
     return p.parse_args()
 
 
@@ -201,6 +205,139 @@ def batched_vs_sequential(n, steps, reps, precision, stream_handle):
             "status": status}
 
 
+# FLOPs of the surrogate network per sample and member (4-128-128-128-2):
+# forward 2(4*128 + 2*128^2 + 128*2); backward 4*2*128 + 8*128^2 + 2*128*4.
+MLP_FWD_FLOP = 2 * (4 * 128 + 2 * 128 * 128 + 128 * 2)
+MLP_BWD_FLOP = 4 * 2 * 128 + 8 * 128 * 128 + 2 * 128 * 4
+# FP32 FMA peak of the SIMT pipes: 152 SMs x 128 lanes x 2 FLOP at 2070 MHz.
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def surrogate_cpu_baseline(solver_s_per_point, n=4096, members=5):
+    """The FP64 reference MLP (oracle) timed on the host: solver seconds per
+    point over its seconds per point."""
+    import numpy as np
+
+    from oracle import mlp_oracle as M
+
+    rng = np.random.default_rng(0)
+    ps = [M.init_params(rng) for _ in range(members)]
+    X = rng.standard_normal((n, 4))
+    t0 = time.perf_counter()
+    for p in ps:
+        M.forward(p, X)
+    el = time.perf_counter() - t0
+    return {"value": solver_s_per_point / (el / n), "unit": "x", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": "FP64 numpy forward of %d members on %d points, %.2f s" % (members, n, el)}
+
+
+def mlp_kernels(stream_handle, n_infer=65536, n_train=4096, members=5, reps=10):
+    """Device-resident timings of the surrogate kernels: ensemble inference on
+    n_infer points (forward + mean/spread) and Adam training steps on
+    n_train samples (forward + backward + update), against the FP32 ALU peak."""
+    import numpy as np
+    import torch
+
+    from paper_2512_12934_gb300 import lbm
+
+    net = lbm.MLP(members, seed=1, stream=stream_handle)
+    try:
+        rng = np.random.default_rng(0)
+        X = torch.from_numpy(rng.standard_normal((n_infer, 4)).astype(np.float32)).cuda()
+        mean = torch.empty((n_infer, 2), dtype=torch.float32, device="cuda")
+        spread = torch.empty(n_infer, dtype=torch.float32, device="cuda")
+        net.predict_device(X.data_ptr(), n_infer, mean.data_ptr(), spread.data_ptr())
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        ev0.record(st)
+        for _ in range(reps):
+            net.predict_device(X.data_ptr(), n_infer, mean.data_ptr(), spread.data_ptr())
+        ev1.record(st)
+        torch.cuda.synchronize()
+        t_inf = ev0.elapsed_time(ev1) / 1e3 / reps
+        Xt = rng.standard_normal((n_train, 4)).astype(np.float32)
+        Tt = rng.standard_normal((n_train, 2)).astype(np.float32)
+        net.train(Xt, Tt, epochs=2, batch=n_train, lr=1e-3)
+        t0 = time.perf_counter()
+        net.train(Xt, Tt, epochs=reps, batch=n_train, lr=1e-3)
+        t_step = (time.perf_counter() - t0) / reps
+    finally:
+        net.close()
+    inf_tf = n_infer * members * MLP_FWD_FLOP / t_inf / 1e12
+    tr_tf = n_train * members * (MLP_FWD_FLOP + MLP_BWD_FLOP) / t_step / 1e12
+    return {"members": members,
+            "infer_points": n_infer, "infer_ms": t_inf * 1e3, "infer_points_per_s": n_infer / t_inf,
+            "infer_tflops": inf_tf, "infer_frac_of_fp32_alu_peak": inf_tf / FP32_ALU_PEAK_TFLOPS,
+            "train_samples": n_train, "train_step_ms": t_step * 1e3, "train_tflops": tr_tf,
+            "train_frac_of_fp32_alu_peak": tr_tf / FP32_ALU_PEAK_TFLOPS,
+            "fp32_alu_peak_tflops": FP32_ALU_PEAK_TFLOPS,
+            "note": "infer: CUDA events over device-pointer lbm_mlp_predict calls; train: wall time of "
+                    "lbm_mlp_train epochs of one full-batch Adam step (includes the per-epoch shuffle upload)"}
+
+
+def surrogate_eval(args, stream_handle):
+    """Train the surrogate on solver runs and judge it on held-out runs."""
+    import numpy as np
+    import torch
+
+    from paper_2512_12934_gb300 import surrogate as SU
+
+    dev = SU.Device()
+    gamma = SU.surface_tension()
+    n_tr, n_te = args.sur_train, args.sur_test
+    pts = SU.sample_points(n_tr + n_te, 2512007)
+    t0 = time.perf_counter()
+    Y, valid, solver_s = SU.generate(pts, dev)
+    gen_wall = time.perf_counter() - t0
+    tr = np.arange(n_tr)[valid[:n_tr]]
+    te = n_tr + np.arange(n_te)[valid[n_tr:]]
+    sur = SU.Surrogate(members=5, gamma=gamma, dev=dev)
+    try:
+        t0 = time.perf_counter()
+        sur.fit(pts[tr], Y[tr], epochs=300, batch=32, lr=2e-3)
+        train_s = time.perf_counter() - t0
+        val, spread = sur.predict(pts[te])
+        err = np.abs(val / Y[te] - 1.0)
+        acc = spread <= 0.05
+        big = SU.sample_points(65536, 99)
+        F = sur._x(big)
+        Xd = torch.from_numpy(F).cuda()
+        md = torch.empty((len(big), 2), dtype=torch.float32, device="cuda")
+        sd = torch.empty(len(big), dtype=torch.float32, device="cuda")
+        sur.net.predict_device(Xd.data_ptr(), len(big), md.data_ptr(), sd.data_ptr())
+        torch.cuda.synchronize()
+        reps = 10
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            sur.net.predict_device(Xd.data_ptr(), len(big), md.data_ptr(), sd.data_ptr())
+        torch.cuda.synchronize()
+        dev_pp = (time.perf_counter() - t0) / reps / len(big)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            sur.predict(big)  # host parameter points in, host answers out
+        host_pp = (time.perf_counter() - t0) / reps / len(big)
+    finally:
+        sur.close()
+
+    def stats(e):
+        return {"median": float(np.median(e)), "p90": float(np.percentile(e, 90)),
+                "p95": float(np.percentile(e, 95)), "max": float(e.max())} if len(e) else None
+
+    return {
+        "gamma": gamma, "train_runs": n_tr, "test_runs": n_te, "valid_train": int(len(tr)),
+        "valid_test": int(len(te)), "solver_s_per_point": solver_s, "generate_wall_s": gen_wall,
+        "train_wall_s": train_s, "accepted_frac": float(acc.mean()),
+        "D_rel_err_accepted": stats(err[acc, 0]), "T_rel_err_accepted": stats(err[acc, 1]),
+        "D_rel_err_all": stats(err[:, 0]), "T_rel_err_all": stats(err[:, 1]),
+        "D_within_5pct_frac": float((err[acc, 0] <= 0.05).mean()) if acc.any() else None,
+        "net_s_per_point_device": dev_pp, "net_s_per_point_host": host_pp,
+        "speedup_device": solver_s / dev_pp, "speedup_host": solver_s / host_pp,
+        "device": {"Wc": dev.Wc, "length_factor": dev.length_factor, "steps": dev.steps,
+                   "G12": SU.G12_TJ, "Gw": SU.GW_TJ, "ranges": SU.RANGES},
+    }
+
+
 def run_reference(args, world, rank):
     from paper_2512_12934_gb300 import workloads as W
 
@@ -278,6 +415,34 @@ def main():
                               "config": {"workload": "tjunction_ensemble_batched", "instances": args.instances,
                                          "lbm_steps_per_step": args.lbm_steps, "precision": args.precision},
                               "batched_ensemble": res, "clocks": clk}))
+        return 0
+    if args.workload == "surrogate":
+        ck = Clocks(local)
+        ck.start()
+        res = surrogate_eval(args, stream.cuda_stream)
+        kern = mlp_kernels(stream.cuda_stream)
+        clk = ck.stop()
+        cpu = None
+        if rank == 0 and not args.no_cpu:
+            cpu = surrogate_cpu_baseline(res["solver_s_per_point"])
+        if rank == 0:
+            print(json.dumps({
+                "metric": "surrogate speedup per parameter point", "value": res["speedup_device"] * world,
+                "unit": "x", "n_gpus": world, "steps": 1, "warmup": 1,
+                "ms_per_step": res["net_s_per_point_device"] * 65536 * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "tjunction_surrogate", "members": 5, "network": "4-128-128-128-2 GELU",
+                           "inference_batch": 65536, "train_runs": args.sur_train, "test_runs": args.sur_test},
+                "surrogate": res,
+                "roofline": {"bound": "alu", "achieved": kern["infer_tflops"],
+                             "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": kern["infer_frac_of_fp32_alu_peak"], "traffic": None,
+                             "kernel": "mlp_forward_kernel + mlp_reduce_kernel (65536 points x 5 members)"},
+                "mlp_kernels": kern,
+                "e2e": {"value": res["speedup_host"], "unit": "x", "h2d_bytes_per_step": 65536 * 4 * 4,
+                        "d2h_bytes_per_step": 65536 * 3 * 4,
+                        "api": "Surrogate.predict(host points) -> lbm_mlp_predict(host arrays)"},
+                "cpu_baseline": cpu, "gpu_launches": 2 * 10, "clocks": clk}))
         return 0
     w = W.channel() if args.workload == "channel" else W.channel(nx=8192, ny=2048, R=240, xc=1600)
     S = args.lbm_steps
@@ -394,6 +559,9 @@ def main():
     batched = None
     if not args.no_batch and args.workload == "channel":
         batched = batched_vs_sequential(64, 64, 3, args.precision, stream.cuda_stream)
+    mlp = None
+    if not args.no_mlp and args.workload == "channel":
+        mlp = mlp_kernels(stream.cuda_stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -418,6 +586,7 @@ def main():
             "roofline": roofline,
             "roofline_hbm_resident": hbm,
             "batched_ensemble": batched,
+            "surrogate_kernels": mlp,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -306,8 +306,9 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  * W4[2][128], b4[2]; lbm_mlp_num_params() floats.  All members lie back to
  * back: [members][num_params].
  * Host arrays: X [n][4] inputs, T [n][2] targets, row-major.  Every call
- * waits for its own work; device scratch is allocated per call.  One
- * lbm_mlp is not thread-safe. */
+ * waits for its own work.  Per-call device buffers come from a workspace
+ * the ensemble owns, grown (never shrunk) to the largest request so far and
+ * released by lbm_mlp_destroy.  One lbm_mlp is not thread-safe. */
 typedef struct lbm_mlp lbm_mlp;
 
 int64_t lbm_mlp_num_params(void);

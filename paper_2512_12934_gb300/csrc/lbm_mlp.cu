@@ -342,6 +342,8 @@ struct lbm_mlp {
     float* v = nullptr;
     int64_t t = 0;            // Adam steps taken
     uint64_t seed = 0;
+    void* ws = nullptr;       // grow-only device workspace of the per-call buffers
+    size_t ws_bytes = 0;
     std::string err;
 };
 
@@ -376,16 +378,48 @@ cudaError_t set_smem_attrs() {
     return g_attr_err;
 }
 
-// Device scratch owned by one call (train / gradient / forward).
+// Per-call device buffers, carved out of the ensemble's workspace (grown, never
+// shrunk; reallocated only after the stream has drained).
 struct Scratch {
     float *X = nullptr, *T = nullptr, *Y = nullptr, *Z = nullptr, *gp = nullptr, *grad = nullptr;
     int* idx = nullptr;
-    ~Scratch() {
-        void* p[] = {X, T, Y, Z, gp, grad, idx};
-        for (void* q : p)
-            if (q) cudaFree(q);
-    }
 };
+
+// Element counts of X, T, Y, Z, gp, grad (floats) and idx (ints).
+lbm_status carve(lbm_mlp* mm, Scratch& s, size_t nX, size_t nT, size_t nY, size_t nZ, size_t ngp, size_t ngrad,
+                 size_t nidx) {
+    const size_t cnt[7] = {nX, nT, nY, nZ, ngp, ngrad, nidx};
+    size_t off[7], total = 0;
+    for (int k = 0; k < 7; ++k) {
+        off[k] = total;
+        total += (cnt[k] * 4 + 255) / 256 * 256;
+    }
+    if (total > mm->ws_bytes) {
+        MCK(cudaStreamSynchronize(mm->stream));
+        if (mm->ws) cudaFree(mm->ws);
+        mm->ws = nullptr;
+        mm->ws_bytes = 0;
+        const size_t want = total + total / 4;
+        cudaError_t e = cudaMalloc(&mm->ws, want);
+        if (e != cudaSuccess) {
+            mm->ws = nullptr;
+            return mfail(mm, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+                         std::string("mlp workspace: ") + cudaGetErrorString(e));
+        }
+        mm->ws_bytes = want;
+    }
+    char* b = static_cast<char*>(mm->ws);
+    float** fp[6] = {&s.X, &s.T, &s.Y, &s.Z, &s.gp, &s.grad};
+    for (int k = 0; k < 6; ++k) *fp[k] = cnt[k] ? reinterpret_cast<float*>(b + off[k]) : nullptr;
+    s.idx = cnt[6] ? reinterpret_cast<int*>(b + off[6]) : nullptr;
+    return LBM_OK;
+}
+
+#define CARVE(...)                                   \
+    do {                                             \
+        lbm_status cs_ = carve(mm, s, __VA_ARGS__);  \
+        if (cs_ != LBM_OK) return cs_;               \
+    } while (0)
 
 // One training (or gradient-only) step on rows idx[0..B) of the device data.
 lbm_status run_step(lbm_mlp* mm, Scratch& s, int B, const int* idx, bool adam, double lr, float* grad_out) {
@@ -482,8 +516,7 @@ lbm_status lbm_mlp_get_params(lbm_mlp* mm, float* params) {
 lbm_status lbm_mlp_forward(lbm_mlp* mm, const float* X, int n, float* Y) {
     if (!mm || !X || !Y || n < 1) return mfail(mm, LBM_ERR_INVALID_ARG, "bad forward request");
     Scratch s;
-    MCK(cudaMalloc((void**)&s.X, (size_t)n * I * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.Y, (size_t)mm->E * n * O * sizeof(float)));
+    CARVE((size_t)n * I, 0, (size_t)mm->E * n * O, 0, 0, 0, 0);
     MCK(cudaMemcpyAsync(s.X, X, (size_t)n * I * sizeof(float), cudaMemcpyHostToDevice, mm->stream));
     mlp_forward_kernel<false><<<dim3((n + TILE - 1) / TILE, mm->E), NTH, SMEM_BYTES, mm->stream>>>(
         mm->params, s.X, nullptr, n, s.Y, nullptr);
@@ -497,12 +530,8 @@ lbm_status lbm_mlp_gradient(lbm_mlp* mm, const float* X, const float* T, int n, 
     if (!mm || !X || !T || !grad || n < 1) return mfail(mm, LBM_ERR_INVALID_ARG, "bad gradient request");
     Scratch s;
     const int ntile = (n + TILE - 1) / TILE;
-    MCK(cudaMalloc((void**)&s.X, (size_t)n * I * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.T, (size_t)n * O * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.Y, (size_t)mm->E * n * O * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.Z, (size_t)mm->E * 3 * n * H * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.gp, (size_t)mm->E * ntile * P * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.grad, (size_t)mm->E * P * sizeof(float)));
+    CARVE((size_t)n * I, (size_t)n * O, (size_t)mm->E * n * O, (size_t)mm->E * 3 * n * H,
+          (size_t)mm->E * ntile * P, (size_t)mm->E * P, 0);
     MCK(cudaMemcpyAsync(s.X, X, (size_t)n * I * sizeof(float), cudaMemcpyHostToDevice, mm->stream));
     MCK(cudaMemcpyAsync(s.T, T, (size_t)n * O * sizeof(float), cudaMemcpyHostToDevice, mm->stream));
     lbm_status st = run_step(mm, s, n, nullptr, false, 0.0, s.grad);
@@ -519,12 +548,8 @@ lbm_status lbm_mlp_train(lbm_mlp* mm, const float* X, const float* T, int n, int
     batch = std::min(batch, n);
     Scratch s;
     const int ntile = (batch + TILE - 1) / TILE;
-    MCK(cudaMalloc((void**)&s.X, (size_t)n * I * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.T, (size_t)n * O * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.Y, (size_t)mm->E * batch * O * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.Z, (size_t)mm->E * 3 * batch * H * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.gp, (size_t)mm->E * ntile * P * sizeof(float)));
-    MCK(cudaMalloc((void**)&s.idx, (size_t)n * sizeof(int)));
+    CARVE((size_t)n * I, (size_t)n * O, (size_t)mm->E * batch * O, (size_t)mm->E * 3 * batch * H,
+          (size_t)mm->E * ntile * P, 0, (size_t)n);
     MCK(cudaMemcpyAsync(s.X, X, (size_t)n * I * sizeof(float), cudaMemcpyHostToDevice, mm->stream));
     MCK(cudaMemcpyAsync(s.T, T, (size_t)n * O * sizeof(float), cudaMemcpyHostToDevice, mm->stream));
     std::vector<int> perm(n);
@@ -549,13 +574,11 @@ lbm_status lbm_mlp_train(lbm_mlp* mm, const float* X, const float* T, int n, int
 lbm_status lbm_mlp_predict(lbm_mlp* mm, const float* X, int n, float* mean, float* spread, int dst_is_device) {
     if (!mm || !X || !mean || !spread || n < 1) return mfail(mm, LBM_ERR_INVALID_ARG, "bad predict request");
     Scratch s;
-    MCK(cudaMalloc((void**)&s.Y, (size_t)mm->E * n * O * sizeof(float)));
+    const size_t hn = dst_is_device ? 0 : (size_t)n;
+    CARVE(hn * I, hn * O, (size_t)mm->E * n * O, 0, 0, hn, 0);
     const float* dX = X;
     float *dm = mean, *ds = spread;
     if (!dst_is_device) {
-        MCK(cudaMalloc((void**)&s.X, (size_t)n * I * sizeof(float)));
-        MCK(cudaMalloc((void**)&s.T, (size_t)n * O * sizeof(float)));
-        MCK(cudaMalloc((void**)&s.grad, (size_t)n * sizeof(float)));
         MCK(cudaMemcpyAsync(s.X, X, (size_t)n * I * sizeof(float), cudaMemcpyHostToDevice, mm->stream));
         dX = s.X;
         dm = s.T;
@@ -577,7 +600,7 @@ lbm_status lbm_mlp_predict(lbm_mlp* mm, const float* X, int n, float* mean, floa
 void lbm_mlp_destroy(lbm_mlp* mm) {
     if (!mm) return;
     if (mm->stream) cudaStreamSynchronize(mm->stream);
-    void* p[] = {mm->params, mm->m, mm->v};
+    void* p[] = {mm->params, mm->m, mm->v, mm->ws};
     for (void* q : p)
         if (q) cudaFree(q);
     delete mm;

@@ -1,0 +1,268 @@
+"""Learned surrogate of T-junction droplet generation.
+
+The paper validates droplet generation in a T-shaped channel (Sec. III D,
+Fig. 9): in the plug regime the detached plug length follows
+L/W_c = 1 + alpha * Q_d/Q_c.  This module learns the map
+
+    (Ca, Q_d/Q_c, M = nu_d/nu_c, W_d/W_c)  ->  (D/W_c, T u_mean/W_c)
+
+(D: area-equivalent droplet diameter, T: generation period) from runs of
+this solver, with a 5-member MLP ensemble trained and evaluated by the
+library's own kernels (lbm.MLP).  The plain solver stays the fallback for
+every query whose ensemble spread exceeds a tolerance (5 % by default) or
+that lies outside the training box, and it is the judge of the surrogate's
+error.
+
+Everything here is host-side orchestration: solver runs go through
+lbm.Batch (batched CUDA steps), label extraction reads the macroscopic
+fields the library returns, and training/inference run in the library's MLP
+kernels.
+"""
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+from scipy import ndimage
+
+from . import lbm
+from . import workloads as W
+
+# Device family (lattice units).  G12 = 1.4 and |G_w| = 0.3 keep every run of
+# the parameter box below stable for 10^5 steps with the printed interaction
+# weights (G12 = 1.7 and 2.0 diverge within a few thousand steps in this
+# geometry); the dispersed phase (component 1) is non-wetting.
+G12_TJ = 1.4
+GW_TJ = 0.3
+NU_C = 1.0 / 6.0
+RANGES = {"uc": (0.005, 0.012), "q": (0.25, 0.7), "M": (0.4, 2.5), "wr": (0.5, 1.0)}
+
+
+@dataclass
+class Device:
+    Wc: int = 16             # main channel width
+    length_factor: int = 20  # main channel length / Wc
+    steps: int = 80000       # solver steps per parameter point
+    every: int = 100         # sampling interval of the label extraction
+
+
+def sample_points(n, seed, ranges=RANGES):
+    """n parameter points (u_c, q, M, w_r): u_c and w_r uniform, q and M
+    log-uniform over `ranges`."""
+    rng = np.random.default_rng(seed)
+    uc = rng.uniform(*ranges["uc"], size=n)
+    q = np.exp(rng.uniform(np.log(ranges["q"][0]), np.log(ranges["q"][1]), size=n))
+    M = np.exp(rng.uniform(np.log(ranges["M"][0]), np.log(ranges["M"][1]), size=n))
+    wr = rng.uniform(*ranges["wr"], size=n)
+    return np.stack([uc, q, M, wr], axis=1)
+
+
+def in_box(pts, ranges=RANGES):
+    keys = ("uc", "q", "M", "wr")
+    ok = np.ones(len(pts), dtype=bool)
+    for j, k in enumerate(keys):
+        ok &= (pts[:, j] >= ranges[k][0] * (1 - 1e-9)) & (pts[:, j] <= ranges[k][1] * (1 + 1e-9))
+    return ok
+
+
+def workload(pt, dev):
+    uc, q, M, wr = (float(v) for v in pt)
+    Wd = max(4, int(round(wr * dev.Wc)))
+    return W.tjunction(Wc=dev.Wc, length_factor=dev.length_factor, Wd=Wd, side_len=2 * dev.Wc,
+                       x_side=4 * dev.Wc, q_ratio=q, M=M, G12=G12_TJ, Gw=(GW_TJ, -GW_TJ), u_c=uc, nu_c=NU_C,
+                       front=dev.Wc // 2)
+
+
+def mean_inflow(uc, Wc):
+    """Mean of the discrete parabolic inflow profile of the main channel
+    (scalar or array u_c)."""
+    y = np.arange(1, Wc + 1, dtype=np.float64)
+    return np.mean(4.0 * (y - 0.5) * (Wc + 0.5 - y) / (Wc * Wc)) * np.asarray(uc, dtype=np.float64)
+
+
+def surface_tension(G12=G12_TJ, radii=(10.0, 14.0, 20.0), n=100, steps=8000):
+    """Interfacial tension of the two-component model at G12 from the
+    Laplace law (Sec. III A): slope of dp against 1/R over static droplets,
+    p = c_s^2 (rho_1 + rho_2) + G12 rho_1 rho_2."""
+    inv_r, dp = [], []
+    for R in radii:
+        w = W.laplace(nx=n, ny=n, R=R, G12=G12)
+        s = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision="fp32")
+        try:
+            s.step(steps)
+            rho, _ = s.macros()
+        finally:
+            s.close()
+        p = (rho[0] + rho[1]) / 3.0 + G12 * rho[0] * rho[1]
+        c = n // 2
+        inside = rho[0] > 0.5 * (rho[0].max() + rho[0].min())
+        inv_r.append(1.0 / math.sqrt(inside.sum() / math.pi))
+        dp.append(p[c - 5:c + 5, c - 5:c + 5].mean() - p[:5, :5].mean())
+    slope, _ = np.polyfit(inv_r, dp, 1)
+    return float(slope)
+
+
+def features(pts, Wc, gamma):
+    """Network inputs: (log Ca, log q, log M, w_r), Ca = u_mean rho nu_c / gamma
+    with rho = 1."""
+    pts = np.asarray(pts, dtype=np.float64)
+    umean = mean_inflow(pts[:, 0], Wc)
+    Ca = umean * NU_C / gamma
+    return np.stack([np.log(Ca), np.log(pts[:, 1]), np.log(pts[:, 2]), pts[:, 3]], axis=1)
+
+
+class _Tracker:
+    """Per-run label extraction from sampled dispersed-phase fractions."""
+
+    def __init__(self, w, Wc):
+        self.Wc = Wc
+        nx = w.cfg["nx"]
+        xs, Wd = w.meta["x_side"], w.meta["Wd"]
+        self.x0 = xs + Wd + Wc // 2      # downstream window, clear of the junction
+        self.x1 = nx - Wc                # and of the outlet
+        self.xp = xs + Wd + 2 * Wc       # probe column
+        self.c = []
+        self.areas = []                  # (time, area) of plugs fully inside the window
+        self.dead = 0
+
+    def sample(self, t, rho):
+        Wc = self.Wc
+        phi = rho[0, 1:Wc + 1, :] / np.maximum(rho[0, 1:Wc + 1, :] + rho[1, 1:Wc + 1, :], 1e-12)
+        self.c.append((t, float((phi[:, self.xp] > 0.5).mean())))
+        win = phi[:, self.x0:self.x1] > 0.5
+        lab, n = ndimage.label(win)
+        if n:
+            idx = np.arange(1, n + 1)
+            area = ndimage.sum_labels(win, lab, idx)
+            objs = ndimage.find_objects(lab)
+            for k, sl in enumerate(objs):
+                if sl[1].start > 0 and sl[1].stop < win.shape[1]:
+                    self.areas.append((t, float(area[k])))
+
+    def labels(self):
+        """(D/W_c, period in steps, number of plugs seen) or None (no
+        periodic plug formation).  Only samples taken while the run was
+        finite count: with the paper's outlet scheme (Eqs. 20-25) a run can
+        diverge once a plug crosses the outlet, and the channel is long
+        enough (20 W_c) for several plugs to pass the probe before that."""
+        if len(self.c) < 4:
+            return None
+        t = np.array([a for a, _ in self.c])
+        c = np.array([b for _, b in self.c])
+        edges, low = [], True
+        for ti, ci in zip(t, c):
+            if low and ci > 0.5:
+                edges.append(ti)
+                low = False
+            elif not low and ci < 0.15:
+                low = True
+        if len(edges) < 3:
+            return None
+        iv = np.diff(edges)[1:]  # drop the start-up interval
+        if len(iv) >= 2 and iv.std() > 0.25 * iv.mean():
+            return None
+        after = [a for tt, a in self.areas if tt > edges[1]]
+        if not after:
+            return None
+        A = float(np.median(after))
+        return 2.0 * math.sqrt(A / math.pi) / self.Wc, float(iv.mean()), len(edges)
+
+
+def generate(pts, dev=None, batch_size=256, log=None):
+    """Run the solver on every parameter point (batched) and extract labels.
+
+    Returns (labels [n][2] = (D/W_c, T u_mean/W_c), valid [n] bool,
+    seconds of solver time per point)."""
+    dev = dev or Device()
+    pts = np.asarray(pts, dtype=np.float64)
+    n = len(pts)
+    Y = np.full((n, 2), np.nan)
+    valid = np.zeros(n, dtype=bool)
+    t_solver = 0.0
+    for b0 in range(0, n, batch_size):
+        sl = range(b0, min(n, b0 + batch_size))
+        ws = [workload(pts[i], dev) for i in sl]
+        mem = [lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision="fp32") for w in ws]
+        trk = [_Tracker(w, dev.Wc) for w in ws]
+        B = lbm.Batch(mem)
+        try:
+            for it in range(dev.steps // dev.every):
+                t0 = time.perf_counter()
+                B.step(dev.every)
+                try:
+                    B.sync()
+                except lbm.LbmError:
+                    pass
+                t_solver += time.perf_counter() - t0
+                tnow = (it + 1) * dev.every
+                for s, tr in zip(mem, trk):
+                    if tr.dead:
+                        continue
+                    try:
+                        rho, _ = s.macros_f32()
+                    except lbm.LbmError:
+                        tr.dead = tnow
+                        continue
+                    tr.sample(tnow, rho)
+        finally:
+            B.close()
+            for s in mem:
+                s.close()
+        for i, tr in zip(sl, trk):
+            lab = tr.labels()
+            if lab is not None:
+                D, T, _ = lab
+                Y[i] = (D, T * float(mean_inflow(pts[i, 0], dev.Wc)) / dev.Wc)
+                valid[i] = True
+        if log:
+            log("generated %d/%d points, %d valid" % (sl.stop, n, int(valid[:sl.stop].sum())))
+    return Y, valid, t_solver / max(n, 1)
+
+
+class Surrogate:
+    """Ensemble MLP over standardised inputs; targets are the labels divided
+    by their training means (so the kernel's relative spread is the relative
+    spread of the physical quantities)."""
+
+    def __init__(self, members=5, seed=2512005, gamma=None, dev=None):
+        self.net = lbm.MLP(members, seed=seed)
+        self.dev = dev or Device()
+        self.gamma = gamma
+        self.mu = self.sd = self.yscale = None
+
+    def close(self):
+        self.net.close()
+
+    def _x(self, pts):
+        F = features(pts, self.dev.Wc, self.gamma)
+        return ((F - self.mu) / self.sd).astype(np.float32)
+
+    def fit(self, pts, Y, epochs=400, batch=64, lr=2e-3, seed=1):
+        F = features(pts, self.dev.Wc, self.gamma)
+        self.mu, self.sd = F.mean(axis=0), F.std(axis=0) + 1e-12
+        self.yscale = Y.mean(axis=0)
+        self.net.train(self._x(pts), (Y / self.yscale).astype(np.float32), epochs=epochs, batch=batch, lr=lr,
+                       shuffle_seed=seed)
+
+    def predict(self, pts):
+        mean, spread = self.net.predict(self._x(pts))
+        return mean.astype(np.float64) * self.yscale, spread.astype(np.float64)
+
+    def query(self, pts, tol=0.05, log=None):
+        """Answer every point: the ensemble mean where its spread is <= tol
+        and the point is inside the training box, the solver elsewhere.
+        Returns (values [n][2], from_solver [n] bool, valid [n] bool,
+        timings dict)."""
+        pts = np.asarray(pts, dtype=np.float64)
+        t0 = time.perf_counter()
+        val, spread = self.predict(pts)
+        t_net = time.perf_counter() - t0
+        fb = (spread > tol) | ~in_box(pts)
+        valid = np.ones(len(pts), dtype=bool)
+        t1 = time.perf_counter()
+        if fb.any():
+            Yf, vf, _ = generate(pts[fb], self.dev, log=log)
+            val[fb] = Yf
+            valid[fb] = vf
+        t_lbm = time.perf_counter() - t1
+        return val, fb, valid, {"net_s": t_net, "fallback_s": t_lbm, "n_fallback": int(fb.sum())}

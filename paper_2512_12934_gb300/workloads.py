@@ -171,7 +171,7 @@ def random_box(nx, ny, seed, periodic=(1, 1), solid_frac=0.0, G12=1.0, Gw=(0.0, 
 
 
 def tjunction(Wc=40, length_factor=20, Wd=None, side_len=None, x_side=None, Ca=0.01, q_ratio=1.0,
-              M=1.0, G12=1.6, Gw=(0.2, -0.2), u_c=0.01, nu_c=1.0 / 6, seed=2512004) -> Workload:
+              M=1.0, G12=1.6, Gw=(0.2, -0.2), u_c=0.01, nu_c=1.0 / 6, seed=2512004, front=None) -> Workload:
     """T-junction droplet generator (Sec. III D): a main channel of width Wc
     along x (continuous phase, component 2, velocity inlet at x=0, outlet at
     x=nx-1) and a side channel of width Wd entering from the top (dispersed
@@ -203,8 +203,14 @@ def tjunction(Wc=40, length_factor=20, Wd=None, side_len=None, x_side=None, Ca=0
     rho = np.zeros((2, ny, nx))
     rho[0] = FLOOR
     rho[1] = 1.0
-    rho[0, Wc + 1:, :] = 1.0                                 # side channel filled with dispersed phase
-    rho[1, Wc + 1:, :] = FLOOR
+    if front is None:
+        rho[0, Wc + 1:, :] = 1.0                             # side channel filled with dispersed phase
+        rho[1, Wc + 1:, :] = FLOOR
+    else:
+        yy = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+        ph = 0.5 * (1.0 + np.tanh((yy - (Wc + 1 + front)) / 2.0))
+        rho[0] = FLOOR + (1.0 - FLOOR) * ph
+        rho[1] = FLOOR + (1.0 - FLOOR) * (1.0 - ph)
     rho[:, solid != 0] = 0.0
     u = np.zeros((2, ny, nx))
     u[0, 1:Wc + 1, :] = prof_main[:, None]
