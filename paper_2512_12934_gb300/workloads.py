@@ -40,7 +40,7 @@ class Workload:
 
     @property
     def nodes(self) -> int:
-        return self.cfg["nx"] * self.cfg["ny"]
+        return self.cfg["nx"] * self.cfg["ny"] * self.cfg.get("nz", 1)
 
     @property
     def fluid_nodes(self) -> int:
@@ -242,3 +242,161 @@ def tjunction_ensemble(n=256, seed=2512004, wc_range=(40, 120), G12=2.0, Gw=(0.2
         w.name = "tjunction_%03d" % j
         out.append(w)
     return out
+
+
+# ---------------------------------------------------------------------------
+# D3Q19 workloads (fields [component or axis][z][y][x]; face lo/hi are pairs
+# over the two tangential axes in x, y, z order)
+# ---------------------------------------------------------------------------
+
+def _base_cfg3(nx, ny, nz, periodic, G12, Gw, nu, s_q=1.2, s_e=0.0, s_eps_mode=1, body=(0.0, 0.0, 0.0)):
+    return {"lattice": "d3q19", "nx": int(nx), "ny": int(ny), "nz": int(nz),
+            "periodic": tuple(bool(p) for p in periodic), "G12": float(G12),
+            "Gw": (float(Gw[0]), float(Gw[1])), "nu": (float(nu[0]), float(nu[1])), "s_e": float(s_e),
+            "s_q": float(s_q), "s_eps_mode": int(s_eps_mode), "body": tuple(float(b) for b in body),
+            "faces": []}
+
+
+def random_box3(nx, ny, nz, seed, periodic=(1, 1, 1), solid_frac=0.0, G12=1.0, Gw=(0.0, 0.0),
+                nu=(0.1, 0.2), u_amp=0.02, rho_lo=0.2, rho_hi=1.0) -> Workload:
+    """Small random 3D state for invariants and parity on ragged grids."""
+    rng = np.random.default_rng(seed)
+    cfg = _base_cfg3(nx, ny, nz, periodic, G12, Gw, nu)
+    solid = (rng.random((nz, ny, nx)) < solid_frac).astype(np.uint8)
+    rho = rng.uniform(rho_lo, rho_hi, size=(2, nz, ny, nx))
+    u = rng.uniform(-u_amp, u_amp, size=(3, nz, ny, nx))
+    rho[:, solid != 0] = 0.0
+    u[:, solid != 0] = 0.0
+    return Workload("random3_%dx%dx%d" % (nx, ny, nz), cfg, solid, rho, u, 0, {})
+
+
+def laplace3(n=32, R=8.0, G12=3.0, nu=(1.0 / 6, 1.0 / 6), seed=2512011, noise=1e-4, width=0.0) -> Workload:
+    """Static droplet in a fully periodic cube (3D Laplace test)."""
+    rng = np.random.default_rng(seed)
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(np.float64)
+    c = n / 2.0
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    phi = 0.5 * (1.0 - np.tanh(2.0 * (r - R) / width)) if width > 0 else (r <= R).astype(np.float64)
+    rho = np.empty((2, n, n, n))
+    rho[0] = FLOOR + (1.0 - FLOOR) * phi
+    rho[1] = FLOOR + (1.0 - FLOOR) * (1.0 - phi)
+    if noise:
+        rho += rng.uniform(-noise, noise, size=rho.shape)
+    cfg = _base_cfg3(n, n, n, (1, 1, 1), G12, (0.0, 0.0), nu)
+    return Workload("laplace3_%d_R%g" % (n, R), cfg, None, rho, np.zeros((3, n, n, n)), 0, {"R": R})
+
+
+def slit3(nx=4, half=8, nz=4, Fb=1e-6, nu=1.0 / 6) -> Workload:
+    """Single-phase flow between two walls (solid planes y = 0 and y = ny-1)
+    driven by a body force along x, periodic in x and z; the halfway walls
+    sit at y = 1/2 and y = ny - 3/2."""
+    ny = 2 * half + 2
+    solid = np.zeros((nz, ny, nx), dtype=np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, ny - 1, :] = 1
+    cfg = _base_cfg3(nx, ny, nz, (1, 0, 1), 0.0, (0.0, 0.0), (nu, nu), body=(Fb, 0.0, 0.0))
+    rho = np.zeros((2, nz, ny, nx))
+    rho[0] = 1.0
+    rho[1] = FLOOR
+    rho[:, solid != 0] = 0.0
+    return Workload("slit3", cfg, solid, rho, np.zeros((3, nz, ny, nx)), 0, {"H": ny - 2, "Fb": Fb, "nu": nu})
+
+
+def _duct_profile(ny, nz, u_max):
+    """Product of parabolas over the open cross-section y, z in [1, n-2]
+    (halfway walls at 1/2 and n-3/2), zero on the wall layers; [nz][ny]."""
+    def par(n):
+        H = n - 2
+        t = np.arange(n, dtype=np.float64)
+        p = 4.0 * (t - 0.5) * (H + 0.5 - t) / (H * H)
+        p[0] = p[-1] = 0.0
+        return p
+    return u_max * np.outer(par(nz), par(ny))
+
+
+def duct3(nx=24, ny=10, nz=9, R=3.0, xc=8.0, u_max=0.01, G12=1.6, Gw=(0.2, -0.2), nu=(1.0 / 10, 1.0 / 6),
+          alpha=True, chi=True, droplet=True, width=3.0, periodic_z=False) -> Workload:
+    """Droplet in a duct along x: solid layers at y = 0, ny-1 (and z = 0,
+    nz-1 unless periodic_z), velocity inlet on x = 0 and convective outlet
+    on x = nx-1 over the whole open cross-section."""
+    solid = np.zeros((nz, ny, nx), dtype=np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, ny - 1, :] = 1
+    if not periodic_z:
+        solid[0, :, :] = 1
+        solid[nz - 1, :, :] = 1
+    cfg = _base_cfg3(nx, ny, nz, (0, 0, int(periodic_z)), G12, Gw, nu)
+    prof = _duct_profile(ny, nz, u_max)
+    if periodic_z:
+        H = ny - 2
+        t = np.arange(ny, dtype=np.float64)
+        p = 4.0 * (t - 0.5) * (H + 0.5 - t) / (H * H)
+        p[0] = p[-1] = 0.0
+        prof = u_max * np.outer(np.ones(nz), p)
+    cfg["faces"] = [
+        {"kind": "inlet", "side": "xmin", "lo": (0, 0), "hi": (ny - 1, nz - 1), "rho_in": (FLOOR, 1.0),
+         "alpha": int(alpha), "chi": 0, "profile": prof},
+        {"kind": "outlet", "side": "xmax", "lo": (0, 0), "hi": (ny - 1, nz - 1), "rho_in": (0.0, 0.0),
+         "alpha": 0, "chi": int(chi), "profile": np.zeros((nz, ny))},
+    ]
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(np.float64)
+    r = np.sqrt((x - xc) ** 2 + (y - (ny - 1) / 2.0) ** 2 + (z - (nz - 1) / 2.0) ** 2)
+    phi = 0.5 * (1.0 - np.tanh(2.0 * (r - R) / width)) if droplet else np.zeros_like(r)
+    rho = np.empty((2, nz, ny, nx))
+    rho[0] = FLOOR + (1.0 - FLOOR) * phi
+    rho[1] = FLOOR + (1.0 - FLOOR) * (1.0 - phi)
+    u = np.zeros((3, nz, ny, nx))
+    u[0] = prof[:, :, None]
+    rho[:, solid != 0] = 0.0
+    u[:, solid != 0] = 0.0
+    return Workload("duct3_%dx%dx%d" % (nx, ny, nz), cfg, solid, rho, u, 0, {"u_max": u_max})
+
+
+def coflow3(nx=512, ny=96, nz=96, r_in=12, wall=2, r_out=46, nozzle=48, q_ratio=0.5, M=0.2, G12=1.6,
+            Gw=(0.2, -0.2), u_c=0.01, nu_c=1.0 / 6) -> Workload:
+    """Coaxial co-flow droplet generator (Sec. III D, Fig. 10): a tube of
+    radius r_out along x; a nozzle (solid shell r_in < r <= r_in + wall)
+    from x = 0 to x = nozzle; the dispersed phase (component 1) enters
+    through the nozzle bore (r <= r_in), the continuous phase (component 2)
+    through the annulus.  One velocity inlet covers x = 0 (per-node speed
+    and composition), one convective outlet covers x = nx-1.  Pipe-flow
+    profiles: Poiseuille in the bore, the annular Poiseuille profile in the
+    annulus, scaled so the dispersed/continuous flow-rate ratio is q_ratio
+    and the continuous peak speed is u_c."""
+    cy, cz = (ny - 1) / 2.0, (nz - 1) / 2.0
+    z, y = np.mgrid[0:nz, 0:ny].astype(np.float64)
+    r = np.sqrt((y - cy) ** 2 + (z - cz) ** 2)
+    sect_solid = r > r_out
+    shell = (r > r_in) & (r <= r_in + wall)
+    solid = np.zeros((nz, ny, nx), dtype=np.uint8)
+    solid[:, :, :] = sect_solid[:, :, None]
+    solid[:, :, :nozzle] |= shell[:, :, None]
+    bore = r <= r_in
+    ann = (r > r_in + wall) & (r <= r_out)
+    a, b = r_in + wall, r_out
+    # annular Poiseuille: u ~ (b^2 - r^2) + (b^2 - a^2) ln(r/b) / ln(b/a)
+    ua = np.where(ann, (b * b - r * r) + (b * b - a * a) * np.log(np.maximum(r, 1e-12) / b) / np.log(b / a), 0.0)
+    ua = u_c * ua / ua.max()
+    ub = np.where(bore, 1.0 - (r / (r_in + 0.5)) ** 2, 0.0)
+    ub *= q_ratio * ua.sum() / ub.sum()
+    prof = ua + ub
+    rprof = np.stack([np.where(bore, 1.0, FLOOR), np.where(bore, FLOOR, 1.0)])
+    cfg = _base_cfg3(nx, ny, nz, (0, 0, 0), G12, Gw, (M * nu_c, nu_c))
+    cfg["faces"] = [
+        {"kind": "inlet", "side": "xmin", "lo": (0, 0), "hi": (ny - 1, nz - 1), "rho_in": (FLOOR, 1.0),
+         "alpha": 1, "chi": 0, "profile": prof, "rho_profile": rprof},
+        {"kind": "outlet", "side": "xmax", "lo": (0, 0), "hi": (ny - 1, nz - 1), "rho_in": (0.0, 0.0),
+         "alpha": 0, "chi": 1, "profile": np.zeros((nz, ny))},
+    ]
+    xx = np.arange(nx, dtype=np.float64)
+    front = 0.5 * (1.0 - np.tanh((xx - nozzle) / 2.0))      # dispersed phase fills the bore up to the tip
+    phi = bore[:, :, None] * front[None, None, :]
+    rho = np.empty((2, nz, ny, nx))
+    rho[0] = FLOOR + (1.0 - FLOOR) * phi
+    rho[1] = FLOOR + (1.0 - FLOOR) * (1.0 - phi)
+    u = np.zeros((3, nz, ny, nx))
+    u[0] = (ua + ub)[:, :, None]
+    rho[:, solid != 0] = 0.0
+    u[:, solid != 0] = 0.0
+    return Workload("coflow3_%dx%dx%d" % (nx, ny, nz), cfg, solid, rho, u, 0,
+                    {"r_in": r_in, "r_out": r_out, "nozzle": nozzle, "q_ratio": q_ratio, "M": M, "u_c": u_c})
