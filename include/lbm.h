@@ -112,6 +112,7 @@ typedef struct {
     double rho_in[2];
     int alpha_correction;
     int chi_correction;
+    const double* rho_profile;
 } lbm_open_bc;
 
 /* Diagnostics (FP64 reductions on the device).

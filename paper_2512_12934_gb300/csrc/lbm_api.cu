@@ -14,6 +14,7 @@
 
 #include "lbm.h"
 #include "lbm_internal.h"
+#include "lbm_d3q19_host.h"
 
 using namespace lbm;
 
@@ -46,6 +47,7 @@ void side_normal(int side, int* ox, int* oy) {
 }  // namespace
 
 struct lbm_ctx {
+    lbm3::Ctx3* d3 = nullptr;  // non-null: a D3Q19 context (lbm_d3q19_host.cu owns it)
     lbm_grid grid{};
     lbm_params params{};
     int nx = 0, ny = 0, pitch = 0;
@@ -1101,6 +1103,7 @@ extern "C" {
 const char* lbm_version(void) { return "paper_2512_12934_gb300 lbm 0.1 (sm_103a)"; }
 
 const char* lbm_last_error(const lbm_ctx* ctx) {
+    if (ctx && ctx->d3) return lbm3::error(ctx->d3);
     if (ctx) return ctx->err.c_str();
     return g_thread_err;
 }
@@ -1112,8 +1115,24 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
     if (!out) return fail(nullptr, LBM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!grid || !params || !rho_init) return fail(nullptr, LBM_ERR_INVALID_ARG, "grid, params and rho_init are required");
-    if (grid->lattice != LBM_D2Q9)
-        return fail(nullptr, LBM_ERR_UNSUPPORTED, "only LBM_D2Q9 is implemented in this build");
+    if (grid->lattice == LBM_D3Q19) {
+        std::string err;
+        lbm3::Ctx3* c3 = nullptr;
+        lbm_status st = lbm3::create(grid, params, bcs, nbc, solid, rho_init, u_init, cuda_stream, &c3, &err);
+        if (st != LBM_OK) return fail(nullptr, st, err);
+        c = new (std::nothrow) lbm_ctx();
+        if (!c) {
+            lbm3::destroy(c3);
+            return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+        }
+        c->d3 = c3;
+        *out = c;
+        return LBM_OK;
+    }
+    if (grid->lattice != LBM_D2Q9) return fail(nullptr, LBM_ERR_INVALID_ARG, "unknown lattice");
+    for (int f = 0; f < nbc; ++f)
+        if (bcs && bcs[f].rho_profile)
+            return fail(nullptr, LBM_ERR_UNSUPPORTED, "rho_profile is implemented for D3Q19 faces only");
     if (grid->nz != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "D2Q9 needs nz == 1");
     if (grid->nx < 5 || grid->ny < 5) return fail(nullptr, LBM_ERR_INVALID_ARG, "every extent must be >= 5");
     if (18LL * ((grid->nx + 31) / 32 * 32) * grid->ny >= (1LL << 31))
@@ -1348,6 +1367,7 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
 
 lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d3) return lbm3::step(c->d3, nsteps);
     if (nsteps < 0) return fail(c, LBM_ERR_INVALID_ARG, "nsteps must be >= 0");
     if (nsteps == 0) return LBM_OK;
     if (c->precision == LBM_FP64) return run_steps<double, double>(c, nsteps);
@@ -1357,6 +1377,7 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
 
 lbm_status lbm_reset(lbm_ctx* c, const double* rho_init, const double* u_init) {
     if (!c || !rho_init) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->d3) return lbm3::reset(c->d3, rho_init, u_init);
     const uint8_t* sol = c->host_solid_in.data();
     if (c->precision == LBM_FP64) return init_state<double, double>(c, rho_init, u_init, sol);
     if (c->precision == LBM_FP32) return init_state<float, float>(c, rho_init, u_init, sol);
@@ -1365,11 +1386,13 @@ lbm_status lbm_reset(lbm_ctx* c, const double* rho_init, const double* u_init) {
 
 lbm_status lbm_sync(lbm_ctx* c) {
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d3) return lbm3::sync(c->d3);
     return check_status(c);
 }
 
 lbm_status lbm_get_macros(lbm_ctx* c, float* rho, float* u, int dst_is_device) {
     if (!c || !rho || !u) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->d3) return lbm3::get_macros(c->d3, rho, u, dst_is_device);
     lbm_status st = check_status(c);
     if (st != LBM_OK) return st;
     if (c->rbytes == 8) return copy_macros<double>(c, rho, u, false, dst_is_device != 0);
@@ -1378,6 +1401,7 @@ lbm_status lbm_get_macros(lbm_ctx* c, float* rho, float* u, int dst_is_device) {
 
 lbm_status lbm_get_macros_f64(lbm_ctx* c, double* rho, double* u) {
     if (!c || !rho || !u) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->d3) return lbm3::get_macros_f64(c->d3, rho, u);
     lbm_status st = check_status(c);
     if (st != LBM_OK) return st;
     if (c->rbytes == 8) return copy_macros<double>(c, rho, u, true, false);
@@ -1386,6 +1410,7 @@ lbm_status lbm_get_macros_f64(lbm_ctx* c, double* rho, double* u) {
 
 lbm_status lbm_get_populations(lbm_ctx* c, double* f) {
     if (!c || !f) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->d3) return lbm3::get_populations(c->d3, f);
     if (c->precision == LBM_FP64) return download_f<double>(c, f);
     if (c->precision == LBM_FP32) return download_f<float>(c, f);
     return download_f<__half>(c, f);
@@ -1393,6 +1418,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* f) {
 
 lbm_status lbm_set_populations(lbm_ctx* c, const double* f) {
     if (!c || !f) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->d3) return lbm3::set_populations(c->d3, f);
     if (c->precision == LBM_FP64) return upload_f<double>(c, f, c->cur);
     if (c->precision == LBM_FP32) return upload_f<float>(c, f, c->cur);
     return upload_f<__half>(c, f, c->cur);
@@ -1400,6 +1426,7 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f) {
 
 lbm_status lbm_get_diagnostics(lbm_ctx* c, lbm_diag* out) {
     if (!c || !out) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->d3) return lbm3::diagnostics(c->d3, out);
     cudaError_t e;
     const int px = c->grid.periodic[0] ? 1 : 0, py = c->grid.periodic[1] ? 1 : 0;
     const void* rr = c->rref[c->cur];
@@ -1460,6 +1487,7 @@ lbm_status lbm_get_diagnostics(lbm_ctx* c, lbm_diag* out) {
 
 lbm_status lbm_save(lbm_ctx* c, const char* path) {
     if (!c || !path) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
     CK(cudaStreamSynchronize(c->stream));
     FILE* fp = std::fopen(path, "wb");
     if (!fp) return fail(c, LBM_ERR_IO, std::string("cannot open ") + path);
@@ -1494,6 +1522,7 @@ lbm_status lbm_save(lbm_ctx* c, const char* path) {
 
 lbm_status lbm_load(lbm_ctx* c, const char* path) {
     if (!c || !path) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(c, LBM_ERR_IO, std::string("cannot open ") + path);
     char magic[8];
@@ -1532,6 +1561,7 @@ lbm_status lbm_load(lbm_ctx* c, const char* path) {
 
 lbm_status lbm_enable_kernel_timing(lbm_ctx* c, int every) {
     if (!c || every < 0) return fail(c, LBM_ERR_INVALID_ARG, "bad timing request");
+    if (c->d3) return lbm3::enable_timing(c->d3, every);
     CK(cudaStreamSynchronize(c->stream));
     c->timing_every = every;
     c->n_samples = 0;
@@ -1548,6 +1578,7 @@ lbm_status lbm_kernel_time(lbm_ctx* c, double* mean_ms, int64_t* samples) {
 
 lbm_status lbm_kernel_time_split(lbm_ctx* c, double* fast_ms, double* general_ms, int64_t* samples) {
     if (!c || !fast_ms || !general_ms || !samples) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->d3) return lbm3::kernel_time_split(c->d3, fast_ms, general_ms, samples);
     CK(cudaStreamSynchronize(c->stream));
     double tf = 0.0, tg = 0.0;
     for (int i = 0; i < c->n_samples; ++i) {
@@ -1565,6 +1596,7 @@ lbm_status lbm_kernel_time_split(lbm_ctx* c, double* fast_ms, double* general_ms
 
 lbm_status lbm_set_tile_variant(lbm_ctx* c, int variant) {
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
     return build_tiles(c, variant, true);
 }
 
@@ -1574,6 +1606,7 @@ lbm_status lbm_tile_stats(lbm_ctx* c, int* variant, int* fast_tiles, int* genera
                           int64_t* general_nodes) {
     if (!c || !variant || !fast_tiles || !general_tiles || !fast_nodes || !general_nodes)
         return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
     *variant = c->variant;
     *fast_tiles = c->nfast;
     *general_tiles = c->ngeneral;
@@ -1584,6 +1617,7 @@ lbm_status lbm_tile_stats(lbm_ctx* c, int* variant, int* fast_tiles, int* genera
 
 lbm_status lbm_set_graph_mode(lbm_ctx* c, int use_graphs) {
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d3) return LBM_OK;  // D3Q19 steps are plain launches
     c->use_graphs = use_graphs ? 1 : 0;
     return LBM_OK;
 }
@@ -1592,6 +1626,9 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int n, void* cuda_stream, l
     if (!out) return bfail(nullptr, LBM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!members || n < 1) return bfail(nullptr, LBM_ERR_INVALID_ARG, "need at least one member");
+    for (int i = 0; i < n; ++i)
+        if (members[i] && members[i]->d3)
+            return bfail(nullptr, LBM_ERR_UNSUPPORTED, "batches of D3Q19 contexts are not implemented");
     for (int i = 0; i < n; ++i) {
         if (!members[i]) return bfail(nullptr, LBM_ERR_INVALID_ARG, "NULL member");
         if (members[i]->precision != members[0]->precision)
@@ -1656,6 +1693,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, int* variant, double* ms_
 
 lbm_status lbm_autotune(lbm_ctx* c, int steps, int* variant, double* ms_per_step) {
     if (!c || !variant || steps < 1) return fail(c, LBM_ERR_INVALID_ARG, "bad autotune request");
+    if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
     lbm_batch* b = nullptr;
     lbm_ctx* one[1] = {c};
     lbm_status st = lbm_batch_create(one, 1, c->stream, &b);
@@ -1697,6 +1735,11 @@ const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str()
 
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
+    if (c->d3) {
+        lbm3::destroy(c->d3);
+        delete c;
+        return;
+    }
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     free_ctx(c);

@@ -1,0 +1,82 @@
+// D3Q19 kernels: argument block, face descriptors and launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace lbm3 {
+
+constexpr int Q = 19;
+
+// Per-node info word: bits 0-18 pull source of direction i blocked
+// (halfway bounce-back or open-face unknown); bit 19 solid; bits 20-22 face
+// id + 1 of an open-face node; bits 23-25 face id + 1 of the face whose
+// inward neighbour this node is; bit 26 a solid site lies within the
+// interaction stencil (adhesion, Eq. 11, is non-zero).
+constexpr uint32_t INFO3_SOLID = 1u << 19;
+constexpr int INFO3_FACE_SHIFT = 20;
+constexpr int INFO3_NBR_SHIFT = 23;
+constexpr uint32_t INFO3_NEAR_SOLID = 1u << 26;
+
+enum { FACE3_INLET = 1, FACE3_OUTLET = 2 };
+// device scalars of the open boundaries (ping-pong per step)
+enum { SC3_LAMBDA = 0, SC3_CHI = 1, SC3_QIN = 2, SC3_QOUT = 3, SC3_UMEAN = 4, SC3_N = 8 };
+
+struct FaceDev3 {
+    int kind, side, axis;  // axis = side / 2
+    int o[3];              // outward unit normal
+    int a0, a1;            // tangential axes (ascending)
+    int lo0, lo1, len0, len1;
+    int base, count;       // slot range [base, base + count)
+    int alpha, chi;
+    double sa[3];          // sum over the unknowns of e_a^2 w (Eq. 19)
+};
+
+// Slot of face position (t0, t1) = the node's tangential coordinates.
+__host__ __device__ inline int face_slot(const FaceDev3& F, int x, int y, int z) {
+    const int c[3] = {x, y, z};
+    return F.base + (c[F.a1] - F.lo1) * F.len0 + (c[F.a0] - F.lo0);
+}
+
+template <typename S>
+struct D3Args {
+    int nx, ny, nz, pitch;
+    long long plane;
+    int periodic[3];
+    int open_side[6];
+    const S* fin;
+    S* fout;
+    const uint32_t* info;
+    S* rho;   // [2][plane] component densities of the step
+    S* umac;  // [3][plane] u^eq of the step (may be null)
+    int nfaces;
+    FaceDev3 face[6];
+    int nface_slots, have_inlet, out_count;
+    const double* face_speed;  // [slots] inward normal speed
+    const double* face_rho;    // [2][slots] inlet composition
+    const uint8_t* face_fluid; // [slots]
+    S* FpF;                    // [slots][2][3] force at the face node (previous step)
+    S* FpN;                    // [slots][2][3] force at its inward neighbour
+    S* fo;                     // [slots][2][19] outlet post-boundary populations of the previous step
+    S* fface;                  // [slots][2][19] post-boundary populations of this step
+    double* flux;              // [slots][2] flux terms of this step
+    const double* scal_in;
+    double* scal_out;
+    unsigned int* status;
+    S G[3];  // G12, G_w,1, G_w,2
+    S body[3];
+    S s[2][Q];
+};
+
+template <typename S>
+cudaError_t launch_step(const D3Args<S>& a, cudaStream_t st, cudaEvent_t mid_a = nullptr,
+                        cudaEvent_t mid_b = nullptr);
+
+// FP64 sums over fluid nodes of each component's populations and the
+// largest |u|^2: partial [nblocks][3].
+template <typename S>
+cudaError_t launch_mass(const S* f, const uint32_t* info, const S* umac, int nx, int ny, int nz, int pitch,
+                        long long plane, double* partial, int nblocks, cudaStream_t st);
+
+}  // namespace lbm3

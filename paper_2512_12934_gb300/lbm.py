@@ -44,7 +44,7 @@ class lbm_open_bc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("side", ctypes.c_int), ("lo", ctypes.c_int * 2),
                 ("hi", ctypes.c_int * 2), ("u_profile", ctypes.POINTER(ctypes.c_double)),
                 ("rho_in", ctypes.c_double * 2), ("alpha_correction", ctypes.c_int),
-                ("chi_correction", ctypes.c_int)]
+                ("chi_correction", ctypes.c_int), ("rho_profile", ctypes.POINTER(ctypes.c_double))]
 
 
 class lbm_diag(ctypes.Structure):
@@ -179,13 +179,17 @@ class Solver:
 
     def __init__(self, cfg, solid, rho_init, u_init=None, precision="fp32", stream=None, rho0_store=1.0):
         L = load()
-        nx, ny = cfg["nx"], cfg["ny"]
-        self.nx, self.ny, self.N = nx, ny, nx * ny
+        three = cfg.get("lattice", "d2q9") == "d3q19"
+        nx, ny, nz = cfg["nx"], cfg["ny"], cfg.get("nz", 1) if three else 1
+        self.nx, self.ny, self.nz, self.N = nx, ny, nz, nx * ny * nz
+        self.dim = 3 if three else 2
+        self.Q = 19 if three else 9
+        self.shape = (nz, ny, nx) if three else (ny, nx)
         g = lbm_grid()
-        g.lattice = LBM_D2Q9
-        g.nx, g.ny, g.nz = nx, ny, 1
-        per = cfg.get("periodic", (0, 0))
-        g.periodic[0], g.periodic[1], g.periodic[2] = int(per[0]), int(per[1]), 0
+        g.lattice = LBM_D3Q19 if three else LBM_D2Q9
+        g.nx, g.ny, g.nz = nx, ny, nz
+        per = tuple(cfg.get("periodic", (0, 0, 0))) + (0, 0, 0)
+        g.periodic[0], g.periodic[1], g.periodic[2] = int(per[0]), int(per[1]), int(per[2]) if three else 0
         p = lbm_params()
         p.G12 = cfg.get("G12", 0.0)
         gw = cfg.get("Gw", (0.0, 0.0))
@@ -194,8 +198,8 @@ class Solver:
         p.s_e = cfg.get("s_e", 0.0)
         p.s_q = cfg.get("s_q", 1.2)
         p.s_eps_mode = int(cfg.get("s_eps_mode", 1))
-        b = cfg.get("body", (0.0, 0.0))
-        p.body_force[0], p.body_force[1], p.body_force[2] = b[0], b[1], 0.0
+        b = tuple(cfg.get("body", (0.0, 0.0))) + (0.0, 0.0, 0.0)
+        p.body_force[0], p.body_force[1], p.body_force[2] = b[0], b[1], b[2] if three else 0.0
         p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         p.rho0_store = rho0_store
         faces = cfg.get("faces", [])
@@ -204,10 +208,26 @@ class Solver:
         for j, fc in enumerate(faces):
             BC[j].kind = LBM_INLET_VELOCITY if fc["kind"] == "inlet" else LBM_OUTLET_CONVECTIVE
             BC[j].side = SIDES[fc["side"]]
-            BC[j].lo[0], BC[j].hi[0] = fc["lo"], fc["hi"]
-            prof = np.ascontiguousarray(fc.get("profile", np.zeros(fc["hi"] - fc["lo"] + 1)), dtype=np.float64)
+            if three:
+                BC[j].lo[0], BC[j].lo[1] = fc["lo"]
+                BC[j].hi[0], BC[j].hi[1] = fc["hi"]
+                npos = (fc["hi"][0] - fc["lo"][0] + 1) * (fc["hi"][1] - fc["lo"][1] + 1)
+            else:
+                BC[j].lo[0], BC[j].hi[0] = fc["lo"], fc["hi"]
+                npos = fc["hi"] - fc["lo"] + 1
+            prof = fc.get("profile")
+            prof = np.zeros(npos) if prof is None else prof
+            prof = np.ascontiguousarray(prof, dtype=np.float64).reshape(-1)
+            if prof.size != npos:
+                raise ValueError("face profile needs %d values" % npos)
             keep.append(prof)
             BC[j].u_profile = _dptr(prof)
+            if fc.get("rho_profile") is not None:
+                rp = np.ascontiguousarray(fc["rho_profile"], dtype=np.float64).reshape(-1)
+                if rp.size != 2 * npos:
+                    raise ValueError("face rho_profile needs %d values" % (2 * npos))
+                keep.append(rp)
+                BC[j].rho_profile = _dptr(rp)
             r = fc.get("rho_in", (0.0, 0.0))
             BC[j].rho_in[0], BC[j].rho_in[1] = r
             BC[j].alpha_correction = int(fc.get("alpha", 1))
@@ -248,27 +268,28 @@ class Solver:
         _check(load().lbm_sync(self.h), self.h)
 
     def macros(self):
-        """(rho[2][ny][nx], u[2][ny][nx]) as float64 on the host."""
+        """(rho[2][...], u[dim][...]) as float64 on the host ([ny][nx] in
+        2D, [nz][ny][nx] in 3D)."""
         rho = np.zeros(2 * self.N)
-        u = np.zeros(2 * self.N)
+        u = np.zeros(self.dim * self.N)
         _check(load().lbm_get_macros_f64(self.h, _dptr(rho), _dptr(u)), self.h)
-        return rho.reshape(2, self.ny, self.nx), u.reshape(2, self.ny, self.nx)
+        return rho.reshape(2, *self.shape), u.reshape(self.dim, *self.shape)
 
     def macros_f32(self, rho_ptr=None, u_ptr=None, device=False):
         """float32 fields into caller buffers (host numpy arrays, or device
         pointers when device=True); returns the numpy arrays if none given."""
         if rho_ptr is None:
             rho = np.zeros(2 * self.N, dtype=np.float32)
-            u = np.zeros(2 * self.N, dtype=np.float32)
+            u = np.zeros(self.dim * self.N, dtype=np.float32)
             _check(load().lbm_get_macros(self.h, rho.ctypes.data, u.ctypes.data, 0), self.h)
-            return rho.reshape(2, self.ny, self.nx), u.reshape(2, self.ny, self.nx)
+            return rho.reshape(2, *self.shape), u.reshape(self.dim, *self.shape)
         _check(load().lbm_get_macros(self.h, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr), int(device)), self.h)
         return None
 
     def populations(self):
-        f = np.zeros(18 * self.N)
+        f = np.zeros(2 * self.Q * self.N)
         _check(load().lbm_get_populations(self.h, _dptr(f)), self.h)
-        return f.reshape(2, 9, self.ny, self.nx)
+        return f.reshape(2, self.Q, *self.shape)
 
     def set_populations(self, f):
         a = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
