@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "lbm_d3q19.h"
 
@@ -91,10 +92,39 @@ __host__ __device__ constexpr int sw5040_(int r2) {
     return r2 == 1 ? 448 : r2 == 2 ? 240 : r2 == 3 ? 96 : r2 == 4 ? 50 : r2 == 5 ? 16 : r2 == 6 ? 8 : r2 == 8 ? 1 : 0;
 }
 
+// Compile-time loop: f(std::integral_constant<int, i>) for i in [B, E), so
+// every lattice constant below is a template constant (no runtime tables).
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// acc += c * v with the integer c folded at compile time (0: nothing).
+template <int c, typename R>
+__device__ __forceinline__ void acc_c(R& acc, R v) {
+    if constexpr (c == 1) acc += v;
+    else if constexpr (c == -1) acc -= v;
+    else if constexpr (c != 0) acc += (R)c * v;
+}
+
 // ---- tiles of the collide kernel -----------------------------------------
 constexpr int TX = 32, TY = 4, TZ = 2;
 constexpr int HX = TX + 4, HY = TY + 4, HZ = TZ + 4;
 constexpr int HN = HX * HY * HZ;
+
+template <typename R>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
+};
 
 template <typename S>
 struct Store;
@@ -116,38 +146,56 @@ __device__ __forceinline__ long long node_index(const D3Args<S>& a, int x, int y
 }
 
 // Pull the 19 populations of component k at (x, y, z) (Eq. 2, Eq. B1, Eq. B2).
+// Away from periodic edges the source of direction i is n minus a fixed
+// offset (e_x + e_y pitch + e_z ny pitch); across an edge it is wrapped.
 template <typename S, typename R>
 __device__ __forceinline__ void pull(const D3Args<S>& a, int k, int x, int y, int z, uint32_t info, R (&f)[Q]) {
     const S* __restrict__ fin = a.fin + (size_t)k * Q * a.plane;
     const long long n = node_index(a, x, y, z);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    const long long sy = a.pitch, sz = (long long)a.ny * a.pitch;
+    const bool wrapped = (info & INFO3_WRAP) != 0;
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
         if (info & (1u << i)) {
             f[i] = (R)fin[(size_t)opp_(i) * a.plane + n];
+        } else if (!wrapped) {
+            long long src = n;
+            if constexpr (ex_(i) != 0) src -= ex_(i);
+            if constexpr (ey_(i) == 1) src -= sy;
+            if constexpr (ey_(i) == -1) src += sy;
+            if constexpr (ez_(i) == 1) src -= sz;
+            if constexpr (ez_(i) == -1) src += sz;
+            f[i] = (R)fin[(size_t)i * a.plane + src];
         } else {
-            const int xs = wrap(x - ex_(i), a.nx), ys = wrap(y - ey_(i), a.ny), zs = wrap(z - ez_(i), a.nz);
+            const int xs = ex_(i) ? wrap(x - ex_(i), a.nx) : x;
+            const int ys = ey_(i) ? wrap(y - ey_(i), a.ny) : y;
+            const int zs = ez_(i) ? wrap(z - ez_(i), a.nz) : z;
             f[i] = (R)fin[(size_t)i * a.plane + node_index(a, xs, ys, zs)];
         }
-    }
+    });
 }
 
 template <typename R>
 __device__ __forceinline__ void feq(R rho, R ux, R uy, R uz, R (&out)[Q]) {
     const R uu = ux * ux + uy * uy + uz * uz;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const R eu = (R)ex_(i) * ux + (R)ey_(i) * uy + (R)ez_(i) * uz;
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        R eu = 0;
+        acc_c<ex_(i)>(eu, ux);
+        acc_c<ey_(i)>(eu, uy);
+        acc_c<ez_(i)>(eu, uz);
         out[i] = rho * ((R)w36_(i) / (R)36) * ((R)1 + (R)3 * eu + (R)4.5 * eu * eu - (R)1.5 * uu);
-    }
+    });
 }
 
 // Density as the rest population plus the sums of opposite pairs.
 template <typename R>
 __device__ __forceinline__ R sum19(const R (&f)[Q]) {
     R s = f[0];
-#pragma unroll
-    for (int i = 1; i < Q; ++i)
-        if (opp_(i) > i) s += f[i] + f[opp_(i)];
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if constexpr (opp_(i) > i) s += f[i] + f[opp_(i)];
+    });
     return s;
 }
 
@@ -156,59 +204,100 @@ __device__ __forceinline__ R sum19(const R (&f)[Q]) {
 template <typename R>
 __device__ __forceinline__ void moments_j(const R (&f)[Q], R& jx, R& jy, R& jz) {
     R x = 0, y = 0, z = 0;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const int o = opp_(i);
-        if (o < i) continue;
-        const R d = f[i] - f[o];
-        if (ex_(i)) x += (R)ex_(i) * d;
-        if (ey_(i)) y += (R)ey_(i) * d;
-        if (ez_(i)) z += (R)ez_(i) * d;
-    }
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if constexpr (opp_(i) > i) {
+            const R d = f[i] - f[opp_(i)];
+            acc_c<ex_(i)>(x, d);
+            acc_c<ey_(i)>(y, d);
+            acc_c<ez_(i)>(z, d);
+        }
+    });
     jx = x;
     jy = y;
     jz = z;
 }
 
-// Eq. 1 for one component: f <- f - T^-1 S T (f - feq) + T^-1 (I - S/2) T Fbar
+// Eq. 1 for one component: f <- f - T^-1 S (T f - m^eq) + T^-1 (I - S/2) F_m,
+// T^-1 = T^T diag(1/|row|^2) (orthogonal rows).  m^eq = T f^eq and F_m =
+// T Fbar (Eqs. 6, 9) are written out as the polynomials they reduce to for
+// this basis (rho; e: rho(19u^2 - 11); eps: rho(6 - 11u^2)/2; j: rho u;
+// q: -2 rho u/3; 3p_xx: rho(3u_x^2 - u^2); 3pi_xx: -3p_xx/2; p_ww:
+// rho(u_y^2 - u_z^2); pi_ww: -p_ww/2; p_ab: rho u_a u_b; m: 0 -- and for
+// F_m the same moments of the Guo term: 0, 38 u.F, -11 u.F, F, -2F/3,
+// 2(3u_xF_x - u.F), -(3u_xF_x - u.F), 2(u_yF_y - u_zF_z), -(u_yF_y - u_zF_z),
+// u_aF_b + u_bF_a, 0).  All entries of T are template constants.
+// Moments through opposite pairs: the even rows of T (rho, e, eps, p, pi)
+// weigh f_i and f_ibar alike, the odd rows (j, q, m) with opposite signs, so
+// T f needs only the pair sums P_i = f_i + f_ibar and differences
+// D_i = f_i - f_ibar (i over one member of each pair), and the back
+// transform splits the same way.
+template <int r>
+__host__ __device__ constexpr bool odd_row() {
+    return r == 3 || r == 4 || r == 5 || r == 6 || r == 7 || r == 8 || r == 16 || r == 17 || r == 18;
+}
+
 template <typename R>
 __device__ __forceinline__ void collide(R (&f)[Q], R rho, R ux, R uy, R uz, R Fx, R Fy, R Fz, const R* s) {
-    R d[Q], fb[Q];
-    feq(rho, ux, uy, uz, d);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        d[i] = f[i] - d[i];
-        const R ex = (R)ex_(i), ey = (R)ey_(i), ez = (R)ez_(i);
-        const R eu = ex * ux + ey * uy + ez * uz;
-        const R ax = (R)3 * (ex - ux) + (R)9 * eu * ex;
-        const R ay = (R)3 * (ey - uy) + (R)9 * eu * ey;
-        const R az = (R)3 * (ez - uz) + (R)9 * eu * ez;
-        fb[i] = ((R)w36_(i) / (R)36) * (ax * Fx + ay * Fy + az * Fz);
-    }
-    R g[Q];
-#pragma unroll
-    for (int r = 0; r < Q; ++r) {
-        R m = 0, mf = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int t = T_(r, i);
-            if (t != 0) {
-                m += (R)t * d[i];
-                mf += (R)t * fb[i];
-            }
+    R P[Q], D[Q];  // only the entries of the first member of each pair are used
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if constexpr (opp_(i) > i) {
+            P[i] = f[i] + f[opp_(i)];
+            D[i] = f[i] - f[opp_(i)];
         }
-        g[r] = (-s[r] * m + ((R)1 - (R)0.5 * s[r]) * mf) / (R)Tnorm_(r);
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    });
+    R m[Q];
+    static_for<0, Q>([&](auto Rr) {
+        constexpr int r = decltype(Rr)::value;
         R acc = 0;
-#pragma unroll
-        for (int r = 0; r < Q; ++r) {
-            const int t = T_(r, i);
-            if (t != 0) acc += (R)t * g[r];
-        }
-        f[i] += acc;
+        if constexpr (!odd_row<r>()) acc_c<T_(r, 0)>(acc, f[0]);
+        static_for<1, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            if constexpr (opp_(i) > i) {
+                if constexpr (odd_row<r>()) acc_c<T_(r, i)>(acc, D[i]);
+                else acc_c<T_(r, i)>(acc, P[i]);
+            }
+        });
+        m[r] = acc;
+    });
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+    const R pxx = (R)2 * ux * ux - uy * uy - uz * uz, fxx = (R)2 * ((R)2 * ux * Fx - uy * Fy - uz * Fz);
+    const R pww = uy * uy - uz * uz, fww = (R)2 * (uy * Fy - uz * Fz);
+    const R meq[Q] = {rho, rho * ((R)19 * uu - (R)11), rho * ((R)6 - (R)11 * uu) * (R)0.5, rho * ux,
+                      -(R)2 / (R)3 * rho * ux, rho * uy, -(R)2 / (R)3 * rho * uy, rho * uz, -(R)2 / (R)3 * rho * uz,
+                      rho * pxx, -(R)0.5 * rho * pxx, rho * pww, -(R)0.5 * rho * pww, rho * ux * uy, rho * uy * uz,
+                      rho * ux * uz, 0, 0, 0};
+    const R mF[Q] = {0, (R)38 * uF, -(R)11 * uF, Fx, -(R)2 / (R)3 * Fx, Fy, -(R)2 / (R)3 * Fy, Fz,
+                     -(R)2 / (R)3 * Fz, fxx, -(R)0.5 * fxx, fww, -(R)0.5 * fww, ux * Fy + uy * Fx, uy * Fz + uz * Fy,
+                     ux * Fz + uz * Fx, 0, 0, 0};
+    R g[Q];
+    static_for<0, Q>([&](auto Rr) {
+        constexpr int r = decltype(Rr)::value;
+        g[r] = (-s[r] * (m[r] - meq[r]) + ((R)1 - (R)0.5 * s[r]) * mF[r]) * ((R)1 / (R)Tnorm_(r));
+    });
+    {
+        R acc = 0;
+        static_for<0, Q>([&](auto Rr) {
+            constexpr int r = decltype(Rr)::value;
+            acc_c<T_(r, 0)>(acc, g[r]);
+        });
+        f[0] += acc;
     }
+    static_for<1, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if constexpr (opp_(i) > i) {
+            R ev = 0, od = 0;
+            static_for<0, Q>([&](auto Rr) {
+                constexpr int r = decltype(Rr)::value;
+                if constexpr (odd_row<r>()) acc_c<T_(r, i)>(od, g[r]);
+                else acc_c<T_(r, i)>(ev, g[r]);
+            });
+            f[i] += ev + od;
+            f[opp_(i)] += ev - od;
+        }
+    });
 }
 
 // ---- kernel A: pull, open faces, densities --------------------------------
@@ -368,36 +457,34 @@ template <typename R, typename Site>
 __device__ __forceinline__ void stencil_sums(Site site, bool adhesion, R (&g1)[3], R (&g2)[3], R (&ad)[3]) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) g1[q] = g2[q] = ad[q] = (R)0;
-#pragma unroll
-    for (int dz = -2; dz <= 2; ++dz)
-#pragma unroll
-        for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-            for (int dx = -2; dx <= 2; ++dx) {
-                const int r2 = dx * dx + dy * dy + dz * dz;
-                const int wq = sw5040_(r2);
-                if (r2 == 0 || wq == 0) continue;
-                const R w = (R)wq / (R)5040;
-                R r1, rr2, sol;
-                site(dx, dy, dz, r1, rr2, sol);
-                if (dx) {
-                    g1[0] += (w * (R)dx) * r1;
-                    g2[0] += (w * (R)dx) * rr2;
-                }
-                if (dy) {
-                    g1[1] += (w * (R)dy) * r1;
-                    g2[1] += (w * (R)dy) * rr2;
-                }
-                if (dz) {
-                    g1[2] += (w * (R)dz) * r1;
-                    g2[2] += (w * (R)dz) * rr2;
-                }
-                if (adhesion) {
-                    if (dx) ad[0] += (w * (R)dx) * sol;
-                    if (dy) ad[1] += (w * (R)dy) * sol;
-                    if (dz) ad[2] += (w * (R)dz) * sol;
-                }
+    static_for<0, 125>([&](auto C) {
+        constexpr int c = decltype(C)::value;
+        constexpr int dx = c % 5 - 2, dy = (c / 5) % 5 - 2, dz = c / 25 - 2;
+        constexpr int r2 = dx * dx + dy * dy + dz * dz;
+        constexpr int wq = sw5040_(r2);
+        if constexpr (r2 != 0 && wq != 0) {
+            const R w = (R)wq / (R)5040;
+            R r1, rr2, sol;
+            site(dx, dy, dz, r1, rr2, sol);
+            if constexpr (dx != 0) {
+                g1[0] += (w * (R)dx) * r1;
+                g2[0] += (w * (R)dx) * rr2;
             }
+            if constexpr (dy != 0) {
+                g1[1] += (w * (R)dy) * r1;
+                g2[1] += (w * (R)dy) * rr2;
+            }
+            if constexpr (dz != 0) {
+                g1[2] += (w * (R)dz) * r1;
+                g2[2] += (w * (R)dz) * rr2;
+            }
+            if (adhesion) {
+                if constexpr (dx != 0) ad[0] += (w * (R)dx) * sol;
+                if constexpr (dy != 0) ad[1] += (w * (R)dy) * sol;
+                if constexpr (dz != 0) ad[2] += (w * (R)dz) * sol;
+            }
+        }
+    });
 }
 
 template <typename R>
@@ -412,108 +499,56 @@ __device__ __forceinline__ void forces(const R* G, R r1, R r2, const R (&g1)[3],
     }
 }
 
-// Force and common velocity of a node from the global density field (used
-// by outlet nodes for the chi rescaling, Eq. 22).
-template <typename S>
-__device__ void node_u_global(const D3Args<S>& a, int x, int y, int z, typename Store<S>::R (&u)[3],
-                              typename Store<S>::R& rt_out) {
-    using R = typename Store<S>::R;
-    const long long n = node_index(a, x, y, z);
-    const uint32_t info = a.info[n];
-    auto site = [&](int dx, int dy, int dz, R& r1, R& r2, R& sol) {
-        const long long m = psi_site(a, x + dx, y + dy, z + dz);
-        if (m < 0) {
-            r1 = r2 = (R)0;
-            sol = (R)1;
-        } else {
-            r1 = a.rho[m];
-            r2 = a.rho[a.plane + m];
-            sol = (R)0;
-        }
-    };
-    R g1[3], g2[3], ad[3];
-    stencil_sums<R>(site, (info & INFO3_NEAR_SOLID) != 0, g1, g2, ad);
-    const R r1 = a.rho[n], r2 = a.rho[a.plane + n];
-    R F1[3], F2[3];
-    forces<R>(a.G, r1, r2, g1, g2, ad, a.body, F1, F2);
-    R f[Q], j[3] = {0, 0, 0};
-    #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        pull<S, R>(a, k, x, y, z, info, f);
-        R jx, jy, jz;
-        moments_j(f, jx, jy, jz);
-        j[0] += jx;
-        j[1] += jy;
-        j[2] += jz;
-    }
-    const R rt = r1 + r2;
-    u[0] = (j[0] + (R)0.5 * (F1[0] + F2[0])) / rt;
-    u[1] = (j[1] + (R)0.5 * (F1[1] + F2[1])) / rt;
-    u[2] = (j[2] + (R)0.5 * (F1[2] + F2[2])) / rt;
-    rt_out = rt;
+template <typename R>
+__device__ __forceinline__ void add_j(const R (&f)[Q], R (&j)[3]) {
+    R jx, jy, jz;
+    moments_j(f, jx, jy, jz);
+    j[0] += jx;
+    j[1] += jy;
+    j[2] += jz;
 }
 
-// Velocity, collision and store of one node whose populations f and forces
-// are known (shared by the interior and the face kernels).
 template <typename S>
-__device__ __forceinline__ void finish_node(const D3Args<S>& a, long long n, typename Store<S>::R (&f)[2][Q],
-                                            typename Store<S>::R r1, typename Store<S>::R r2,
-                                            const typename Store<S>::R (&F1)[3], const typename Store<S>::R (&F2)[3],
-                                            typename Store<S>::R (&u)[3]) {
-    using R = typename Store<S>::R;
-    if (!(isfinite((double)(r1 + r2)) && isfinite((double)u[0]) && isfinite((double)u[1]) &&
-          isfinite((double)u[2])))
+__device__ __forceinline__ void store_pop(const D3Args<S>& a, int k, long long n, const typename Store<S>::R (&f)[Q]) {
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        a.fout[(size_t)(k * Q + i) * a.plane + n] = (S)f[i];
+    });
+}
+
+template <typename S>
+__device__ __forceinline__ void check_store_u(const D3Args<S>& a, long long n, typename Store<S>::R rt,
+                                              const typename Store<S>::R (&u)[3]) {
+    if (!(isfinite((float)rt) && isfinite((float)u[0]) && isfinite((float)u[1]) && isfinite((float)u[2])))
         atomicOr(a.status, 1u);
     if (a.umac) {
         a.umac[n] = u[0];
         a.umac[a.plane + n] = u[1];
         a.umac[2 * a.plane + n] = u[2];
     }
-    collide<R>(f[0], r1, u[0], u[1], u[2], F1[0], F1[1], F1[2], a.s[0]);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) a.fout[(size_t)i * a.plane + n] = (S)f[0][i];
-    collide<R>(f[1], r2, u[0], u[1], u[2], F2[0], F2[1], F2[2], a.s[1]);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) a.fout[(size_t)(Q + i) * a.plane + n] = (S)f[1][i];
 }
 
-template <typename R>
-__device__ __forceinline__ void common_u(const R (&f)[2][Q], R r1, R r2, const R (&F1)[3], const R (&F2)[3],
-                                         R (&u)[3]) {
-    R j[3] = {0, 0, 0};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        R jx, jy, jz;
-        moments_j(f[k], jx, jy, jz);
-        j[0] += jx;
-        j[1] += jy;
-        j[2] += jz;
-    }
-    const R rt = r1 + r2;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) u[q] = (j[q] + (R)0.5 * (F1[q] + F2[q])) / rt;
-}
-
+// Every fluid node of a 32x4x2 tile: forces from the staged densities (the
+// halo resolves periodic wraps and the ghost mirrors of Eqs. 24-25), the
+// common velocity, the collision.  Open-face nodes take their post-boundary
+// populations from the face kernel; outlet nodes stop after the force (their
+// normal velocity waits for the inward neighbour's, Eq. 22), and the inward
+// neighbours of the outlet hand theirs over with the flux terms of Eqs. 21, 23.
 template <typename S>
 __global__ void __launch_bounds__(256) d3q_collide_kernel(D3Args<S> a) {
     using R = typename Store<S>::R;
-    __shared__ R s_r1[HN];
-    __shared__ R s_r2[HN];
+    __shared__ typename Pair<R>::type s_rr[HN];  // (rho_1, rho_2) of the tile and its halo
     __shared__ unsigned char s_sol[HN];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
     for (int q = tid; q < HN; q += TX * TY * TZ) {
         const int hx = q % HX, hy = (q / HX) % HY, hz = q / (HX * HY);
         const long long m = psi_site(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz);
-        if (m < 0) {
-            s_r1[q] = (R)0;
-            s_r2[q] = (R)0;
-            s_sol[q] = 1;
-        } else {
-            s_r1[q] = a.rho[m];
-            s_r2[q] = a.rho[a.plane + m];
-            s_sol[q] = 0;
-        }
+        typename Pair<R>::type v;
+        v.x = m < 0 ? (R)0 : a.rho[m];
+        v.y = m < 0 ? (R)0 : a.rho[a.plane + m];
+        s_rr[q] = v;
+        s_sol[q] = m < 0 ? 1 : 0;
     }
     __syncthreads();
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
@@ -521,93 +556,132 @@ __global__ void __launch_bounds__(256) d3q_collide_kernel(D3Args<S> a) {
     const long long n = node_index(a, x, y, z);
     const uint32_t info = a.info[n];
     if (info & INFO3_SOLID) return;
-    if ((info >> INFO3_FACE_SHIFT) & 7u) return;  // open-face nodes: d3q_face_collide_kernel
     const int hc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (threadIdx.z + 2));
     auto site = [&](int dx, int dy, int dz, R& r1, R& r2, R& sol) {
         const int h = hc + dx + HX * (dy + HY * dz);
-        r1 = s_r1[h];
-        r2 = s_r2[h];
+        const typename Pair<R>::type v = s_rr[h];
+        r1 = v.x;
+        r2 = v.y;
         sol = (R)s_sol[h];
     };
     R g1[3], g2[3], ad[3];
     stencil_sums<R>(site, (info & INFO3_NEAR_SOLID) != 0, g1, g2, ad);
-    const R r1 = s_r1[hc], r2 = s_r2[hc];
+    const R r1 = s_rr[hc].x, r2 = s_rr[hc].y;
     R F1[3], F2[3];
     forces<R>(a.G, r1, r2, g1, g2, ad, a.body, F1, F2);
+    const R rt = r1 + r2;
+    const int fid = (int)((info >> INFO3_FACE_SHIFT) & 7u);
     const int nid = (int)((info >> INFO3_NBR_SHIFT) & 7u);
-    if (nid != 0) {  // force the inlet reconstruction of the next step uses (Eq. 13)
-        const FaceDev3& Fc = a.face[nid - 1];
-        R* Fp = a.FpN + (size_t)face_slot(Fc, x + Fc.o[0], y + Fc.o[1], z + Fc.o[2]) * 6;
+    R f[Q];
+    R j[3] = {0, 0, 0};
+    int slot = -1;
+    if (fid == 0) {
+        pull<S, R>(a, 0, x, y, z, info, f);
+        add_j(f, j);
+        pull<S, R>(a, 1, x, y, z, info, f);
+        add_j(f, j);
+    } else {
+        const FaceDev3& Fc = a.face[fid - 1];
+        slot = face_slot(Fc, x, y, z);
+        R* Fp = a.FpF + (size_t)slot * 6;  // this step's force: next step's inlet, this step's outlet
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             Fp[q] = F1[q];
             Fp[3 + q] = F2[q];
         }
+        if (Fc.kind == FACE3_OUTLET) return;  // finished by d3q_outlet_kernel
+        const R* ff = a.fface + (size_t)slot * 2 * Q;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            static_for<0, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                f[i] = ff[k * Q + i];
+            });
+            add_j(f, j);
+        }
     }
-    R f[2][Q];
-    pull<S, R>(a, 0, x, y, z, info, f[0]);
-    pull<S, R>(a, 1, x, y, z, info, f[1]);
     R u[3];
-    common_u(f, r1, r2, F1, F2, u);
-    finish_node<S>(a, n, f, r1, r2, F1, F2, u);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) u[q] = (j[q] + (R)0.5 * (F1[q] + F2[q])) / rt;
+    if (nid != 0) {
+        const FaceDev3& Fc = a.face[nid - 1];
+        const int ns = face_slot(Fc, x + Fc.o[0], y + Fc.o[1], z + Fc.o[2]);
+        R* Fp = a.FpN + (size_t)ns * 6;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            Fp[q] = F1[q];
+            Fp[3 + q] = F2[q];
+        }
+        if (Fc.kind == FACE3_OUTLET) {
+            const double sg = (double)(Fc.o[0] + Fc.o[1] + Fc.o[2]);
+            R* un = a.unbr + (size_t)ns * 3;
+            un[0] = u[0];
+            un[1] = u[1];
+            un[2] = u[2];
+            a.flux[(size_t)ns * 2 + 0] = (double)rt * sg * (double)u[Fc.axis];
+            a.flux[(size_t)ns * 2 + 1] = sg * (double)u[Fc.axis];
+        }
+    }
+    if (fid != 0) {  // inlet node: flux term of Q_in
+        const FaceDev3& Fc = a.face[fid - 1];
+        const double sg = (double)(Fc.o[0] + Fc.o[1] + Fc.o[2]);
+        a.flux[(size_t)slot * 2 + 0] = (double)rt * (-sg) * (double)u[Fc.axis];
+        a.flux[(size_t)slot * 2 + 1] = 0.0;
+    }
+    check_store_u<S>(a, n, rt, u);
+    // collide component 1 (still in registers), then reload component 0
+    collide<R>(f, r2, u[0], u[1], u[2], F2[0], F2[1], F2[2], a.s[1]);
+    store_pop<S>(a, 1, n, f);
+    if (fid == 0) {
+        pull<S, R>(a, 0, x, y, z, info, f);
+    } else {
+        const R* ff = a.fface + (size_t)slot * 2 * Q;
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            f[i] = ff[i];
+        });
+    }
+    collide<R>(f, r1, u[0], u[1], u[2], F1[0], F1[1], F1[2], a.s[0]);
+    store_pop<S>(a, 0, n, f);
 }
 
-// One thread per face slot: forces from the global density field, chi at the
-// outlet (Eq. 22), flux terms, the collision.
+// One thread per outlet slot: the outlet node's velocity with the normal
+// component chi times that of its inward neighbour (Eq. 22), the collision.
 template <typename S>
-__global__ void __launch_bounds__(128) d3q_face_collide_kernel(D3Args<S> a) {
+__global__ void __launch_bounds__(128) d3q_outlet_kernel(D3Args<S> a) {
     using R = typename Store<S>::R;
     int fid, c[3];
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     if (!slot_node(a, slot, fid, c)) return;
     const FaceDev3& Fc = a.face[fid];
-    const int x = c[0], y = c[1], z = c[2];
-    const long long n = node_index(a, x, y, z);
-    const uint32_t info = a.info[n];
-    auto site = [&](int dx, int dy, int dz, R& r1, R& r2, R& sol) {
-        const long long m = psi_site(a, x + dx, y + dy, z + dz);
-        if (m < 0) {
-            r1 = r2 = (R)0;
-            sol = (R)1;
-        } else {
-            r1 = a.rho[m];
-            r2 = a.rho[a.plane + m];
-            sol = (R)0;
-        }
-    };
-    R g1[3], g2[3], ad[3];
-    stencil_sums<R>(site, (info & INFO3_NEAR_SOLID) != 0, g1, g2, ad);
-    const R r1 = a.rho[n], r2 = a.rho[a.plane + n];
-    R F1[3], F2[3];
-    forces<R>(a.G, r1, r2, g1, g2, ad, a.body, F1, F2);
-    R f[2][Q];
+    if (Fc.kind != FACE3_OUTLET) return;
+    const long long n = node_index(a, c[0], c[1], c[2]);
+    const R r1 = a.rho[n], r2 = a.rho[a.plane + n], rt = r1 + r2;
+    const R* Fp = a.FpF + (size_t)slot * 6;
+    const R F1[3] = {Fp[0], Fp[1], Fp[2]}, F2[3] = {Fp[3], Fp[4], Fp[5]};
     const R* ff = a.fface + (size_t)slot * 2 * Q;
+    R f[Q], j[3] = {0, 0, 0};
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        f[0][i] = ff[i];
-        f[1][i] = ff[Q + i];
+    for (int k = 0; k < 2; ++k) {
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            f[i] = ff[k * Q + i];
+        });
+        add_j(f, j);
     }
     R u[3];
-    common_u(f, r1, r2, F1, F2, u);
-    const int ax = Fc.axis;
-    const double sgn = (double)(Fc.o[0] + Fc.o[1] + Fc.o[2]);  // +1 on a far side, -1 on a near side
-    if (Fc.kind == FACE3_OUTLET) {
-        R un[3], rtn;
-        node_u_global<S>(a, x - Fc.o[0], y - Fc.o[1], z - Fc.o[2], un, rtn);
-        a.flux[(size_t)slot * 2 + 0] = (double)rtn * sgn * (double)un[ax];
-        a.flux[(size_t)slot * 2 + 1] = sgn * (double)un[ax];
-        if (Fc.chi) u[ax] = (R)a.scal_in[SC3_CHI] * un[ax];
-    } else {
-        a.flux[(size_t)slot * 2 + 0] = (double)(r1 + r2) * (-sgn) * (double)u[ax];
-        a.flux[(size_t)slot * 2 + 1] = 0.0;
-    }
-    R* Fp = a.FpF + (size_t)slot * 6;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        Fp[q] = F1[q];
-        Fp[3 + q] = F2[q];
-    }
-    finish_node<S>(a, n, f, r1, r2, F1, F2, u);
+    for (int q = 0; q < 3; ++q) u[q] = (j[q] + (R)0.5 * (F1[q] + F2[q])) / rt;
+    if (Fc.chi) u[Fc.axis] = (R)a.scal_in[SC3_CHI] * a.unbr[(size_t)slot * 3 + Fc.axis];
+    check_store_u<S>(a, n, rt, u);
+    collide<R>(f, r2, u[0], u[1], u[2], F2[0], F2[1], F2[2], a.s[1]);
+    store_pop<S>(a, 1, n, f);
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        f[i] = ff[i];
+    });
+    collide<R>(f, r1, u[0], u[1], u[2], F1[0], F1[1], F1[2], a.s[0]);
+    store_pop<S>(a, 0, n, f);
 }
 
 // ---- kernel C: lambda and chi from the face flux terms (fixed order) -------
@@ -715,7 +789,7 @@ cudaError_t launch_step(const D3Args<S>& a, cudaStream_t st, cudaEvent_t mid_a, 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (mid_b) cudaEventRecord(mid_b, st);
     if (a.nface_slots > 0) {
-        d3q_face_collide_kernel<S><<<fblocks, 128, 0, st>>>(a);
+        d3q_outlet_kernel<S><<<fblocks, 128, 0, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         d3q_reduce_kernel<S><<<1, 256, 0, st>>>(a);
         e = cudaGetLastError();

@@ -18,6 +18,9 @@ constexpr uint32_t INFO3_SOLID = 1u << 19;
 constexpr int INFO3_FACE_SHIFT = 20;
 constexpr int INFO3_NBR_SHIFT = 23;
 constexpr uint32_t INFO3_NEAR_SOLID = 1u << 26;
+// bit 27: a pull source lies across a periodic edge (the plain index offset
+// of a direction does not apply)
+constexpr uint32_t INFO3_WRAP = 1u << 27;
 
 enum { FACE3_INLET = 1, FACE3_OUTLET = 2 };
 // device scalars of the open boundaries (ping-pong per step)
@@ -60,6 +63,7 @@ struct D3Args {
     S* FpN;                    // [slots][2][3] force at its inward neighbour
     S* fo;                     // [slots][2][19] outlet post-boundary populations of the previous step
     S* fface;                  // [slots][2][19] post-boundary populations of this step
+    S* unbr;                   // [slots][3] u^eq of the outlet's inward neighbours (Eq. 22)
     double* flux;              // [slots][2] flux terms of this step
     const double* scal_in;
     double* scal_out;

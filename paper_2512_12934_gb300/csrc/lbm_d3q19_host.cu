@@ -58,6 +58,7 @@ struct Ctx3 {
     void* FpN = nullptr;
     void* fo = nullptr;
     void* fface = nullptr;
+    void* unbr = nullptr;
     double* flux = nullptr;
     double* scal[2] = {nullptr, nullptr};
     unsigned int* status = nullptr;
@@ -146,6 +147,7 @@ void fill_args(const Ctx3* c, D3Args<T>& a, bool write_u) {
     a.FpN = static_cast<T*>(c->FpN);
     a.fo = static_cast<T*>(c->fo);
     a.fface = static_cast<T*>(c->fface);
+    a.unbr = static_cast<T*>(c->unbr);
     a.flux = c->flux;
     a.scal_in = c->scal[c->step & 1];
     a.scal_out = c->scal[(c->step + 1) & 1];
@@ -228,7 +230,7 @@ void destroy(Ctx3* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     void* p[] = {c->f[0], c->f[1], c->info, c->rho, c->umac, c->face_speed, c->face_rho, c->face_fluid, c->FpF,
-                 c->FpN, c->fo, c->fface, c->flux, c->scal[0], c->scal[1], c->status, c->mass_partial};
+                 c->FpN, c->fo, c->fface, c->unbr, c->flux, c->scal[0], c->scal[1], c->status, c->mass_partial};
     for (void* q : p)
         if (q) cudaFree(q);
     for (cudaEvent_t e : c->ev)
@@ -408,7 +410,10 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
                     for (int a = 0; a < 3 && !blocked; ++a) {
                         if (pp[a] >= 0 && pp[a] < ext[a]) continue;
                         if (!c->periodic[a]) blocked = true;
-                        else pp[a] = (pp[a] + ext[a]) % ext[a];
+                        else {
+                            pp[a] = (pp[a] + ext[a]) % ext[a];
+                            w |= INFO3_WRAP;
+                        }
                     }
                     if (!blocked && c->solid[hidx(c, pp[0], pp[1], pp[2])]) blocked = true;
                     if (blocked) w |= 1u << i;
@@ -444,6 +449,7 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
     alloc(&c->FpN, (size_t)slots * 6 * c->sb);
     alloc(&c->fo, (size_t)slots * 2 * Q * c->sb);
     alloc(&c->fface, (size_t)slots * 2 * Q * c->sb);
+    alloc(&c->unbr, (size_t)slots * 3 * c->sb);
     alloc((void**)&c->flux, (size_t)slots * 2 * sizeof(double));
     alloc((void**)&c->scal[0], SC3_N * sizeof(double));
     alloc((void**)&c->scal[1], SC3_N * sizeof(double));
