@@ -388,8 +388,8 @@ __global__ void __launch_bounds__(256) d3q_pull_kernel(D3Args<S> a) {
     if (x >= a.nx || y >= a.ny || z >= a.nz) return;
     const long long n = node_index(a, x, y, z);
     const uint32_t info = a.info[n];
-    if (info & INFO3_SOLID) {
-        a.rho[n] = (R)0;
+    if (info & INFO3_SOLID) {  // rho_1 = SOLID_MARK flags a solid site for the force stencil (psi = 0 there)
+        a.rho[n] = (R)SOLID_MARK;
         a.rho[a.plane + n] = (R)0;
         return;
     }
@@ -434,9 +434,12 @@ __global__ void __launch_bounds__(128) d3q_face_pull_kernel(D3Args<S> a) {
 }
 
 // ---- kernel B: forces, velocity, collision --------------------------------
-// Resolve a psi / indicator site (Eqs. 10, 11, 24, 25): -1 = solid.
+// Resolve a psi / indicator site (Eqs. 10, 11, 24, 25) to a node index:
+// periodic wrap, ghost mirror across open sides, -1 outside a closed side
+// (a solid wall).  Solid nodes inside the grid carry rho_1 = SOLID_MARK, a
+// value no density reaches (the minor component can dip slightly below 0).
 template <typename S>
-__device__ __forceinline__ long long psi_site(const D3Args<S>& a, int x, int y, int z) {
+__device__ __forceinline__ long long site_index(const D3Args<S>& a, int x, int y, int z) {
     int c[3] = {x, y, z};
     const int ext[3] = {a.nx, a.ny, a.nz};
 #pragma unroll
@@ -447,16 +450,15 @@ __device__ __forceinline__ long long psi_site(const D3Args<S>& a, int x, int y, 
         else if (c[ax] >= ext[ax] && a.open_side[2 * ax + 1]) c[ax] = 2 * ext[ax] - 1 - c[ax];
         else return -1;
     }
-    const long long n = node_index(a, c[0], c[1], c[2]);
-    return (a.info[n] & INFO3_SOLID) ? -1 : n;
+    return node_index(a, c[0], c[1], c[2]);
 }
 
 // Interaction sums over the 92-vector stencil: g_k = sum w psi_k(x+e) e,
-// ad = sum w s(x+e) e.  `site(dx, dy, dz, r1, r2, sol)` supplies a site.
+// `site(dx, dy, dz, r1, r2)` supplies the densities of a site (0 at solids).
 template <typename R, typename Site>
-__device__ __forceinline__ void stencil_sums(Site site, bool adhesion, R (&g1)[3], R (&g2)[3], R (&ad)[3]) {
+__device__ __forceinline__ void stencil_sums(Site site, R (&g1)[3], R (&g2)[3]) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) g1[q] = g2[q] = ad[q] = (R)0;
+    for (int q = 0; q < 3; ++q) g1[q] = g2[q] = (R)0;
     static_for<0, 125>([&](auto C) {
         constexpr int c = decltype(C)::value;
         constexpr int dx = c % 5 - 2, dy = (c / 5) % 5 - 2, dz = c / 25 - 2;
@@ -464,8 +466,8 @@ __device__ __forceinline__ void stencil_sums(Site site, bool adhesion, R (&g1)[3
         constexpr int wq = sw5040_(r2);
         if constexpr (r2 != 0 && wq != 0) {
             const R w = (R)wq / (R)5040;
-            R r1, rr2, sol;
-            site(dx, dy, dz, r1, rr2, sol);
+            R r1, rr2;
+            site(dx, dy, dz, r1, rr2);
             if constexpr (dx != 0) {
                 g1[0] += (w * (R)dx) * r1;
                 g2[0] += (w * (R)dx) * rr2;
@@ -478,13 +480,22 @@ __device__ __forceinline__ void stencil_sums(Site site, bool adhesion, R (&g1)[3
                 g1[2] += (w * (R)dz) * r1;
                 g2[2] += (w * (R)dz) * rr2;
             }
-            if (adhesion) {
-                if constexpr (dx != 0) ad[0] += (w * (R)dx) * sol;
-                if constexpr (dy != 0) ad[1] += (w * (R)dy) * sol;
-                if constexpr (dz != 0) ad[2] += (w * (R)dz) * sol;
-            }
         }
     });
+}
+
+// sum_e w s(x+e) e of Eq. 11 (geometry only; precomputed per near-solid node)
+template <typename S>
+__device__ __forceinline__ void adhesion_vector(const D3Args<S>& a, long long n, uint32_t info,
+                                                typename Store<S>::R (&ad)[3]) {
+    using R = typename Store<S>::R;
+    if (info & INFO3_NEAR_SOLID) {
+        ad[0] = (R)a.adv[n];
+        ad[1] = (R)a.adv[a.plane + n];
+        ad[2] = (R)a.adv[2 * a.plane + n];
+    } else {
+        ad[0] = ad[1] = ad[2] = (R)0;
+    }
 }
 
 template <typename R>
@@ -537,18 +548,17 @@ __device__ __forceinline__ void check_store_u(const D3Args<S>& a, long long n, t
 template <typename S>
 __global__ void __launch_bounds__(256) d3q_collide_kernel(D3Args<S> a) {
     using R = typename Store<S>::R;
-    __shared__ typename Pair<R>::type s_rr[HN];  // (rho_1, rho_2) of the tile and its halo
-    __shared__ unsigned char s_sol[HN];
+    __shared__ typename Pair<R>::type s_rr[HN];  // (rho_1, rho_2) of the tile and its halo, psi = 0 at solids
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
     for (int q = tid; q < HN; q += TX * TY * TZ) {
         const int hx = q % HX, hy = (q / HX) % HY, hz = q / (HX * HY);
-        const long long m = psi_site(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz);
+        const long long m = site_index(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz);
         typename Pair<R>::type v;
-        v.x = m < 0 ? (R)0 : a.rho[m];
+        v.x = m < 0 ? (R)SOLID_MARK : a.rho[m];
         v.y = m < 0 ? (R)0 : a.rho[a.plane + m];
+        if (v.x < (R)(0.5 * SOLID_MARK)) v.x = (R)0;
         s_rr[q] = v;
-        s_sol[q] = m < 0 ? 1 : 0;
     }
     __syncthreads();
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
@@ -557,26 +567,25 @@ __global__ void __launch_bounds__(256) d3q_collide_kernel(D3Args<S> a) {
     const uint32_t info = a.info[n];
     if (info & INFO3_SOLID) return;
     const int hc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (threadIdx.z + 2));
-    auto site = [&](int dx, int dy, int dz, R& r1, R& r2, R& sol) {
-        const int h = hc + dx + HX * (dy + HY * dz);
-        const typename Pair<R>::type v = s_rr[h];
+    auto site = [&](int dx, int dy, int dz, R& r1, R& r2) {
+        const typename Pair<R>::type v = s_rr[hc + dx + HX * (dy + HY * dz)];
         r1 = v.x;
         r2 = v.y;
-        sol = (R)s_sol[h];
     };
-    R g1[3], g2[3], ad[3];
-    stencil_sums<R>(site, (info & INFO3_NEAR_SOLID) != 0, g1, g2, ad);
-    const R r1 = s_rr[hc].x, r2 = s_rr[hc].y;
-    R F1[3], F2[3];
-    forces<R>(a.G, r1, r2, g1, g2, ad, a.body, F1, F2);
-    const R rt = r1 + r2;
     const int fid = (int)((info >> INFO3_FACE_SHIFT) & 7u);
     const int nid = (int)((info >> INFO3_NBR_SHIFT) & 7u);
     R f[Q];
     R j[3] = {0, 0, 0};
     int slot = -1;
+    if (fid == 0) pull<S, R>(a, 0, x, y, z, info, f);  // loads overlap the stencil below
+    R g1[3], g2[3], ad[3];
+    stencil_sums<R>(site, g1, g2);
+    adhesion_vector<S>(a, n, info, ad);
+    const R r1 = s_rr[hc].x, r2 = s_rr[hc].y;
+    R F1[3], F2[3];
+    forces<R>(a.G, r1, r2, g1, g2, ad, a.body, F1, F2);
+    const R rt = r1 + r2;
     if (fid == 0) {
-        pull<S, R>(a, 0, x, y, z, info, f);
         add_j(f, j);
         pull<S, R>(a, 1, x, y, z, info, f);
         add_j(f, j);

@@ -23,6 +23,8 @@ constexpr uint32_t INFO3_NEAR_SOLID = 1u << 26;
 constexpr uint32_t INFO3_WRAP = 1u << 27;
 
 enum { FACE3_INLET = 1, FACE3_OUTLET = 2 };
+// rho_1 of solid nodes in the density field (read as psi = 0, s = 1)
+constexpr double SOLID_MARK = -1.0e30;
 // device scalars of the open boundaries (ping-pong per step)
 enum { SC3_LAMBDA = 0, SC3_CHI = 1, SC3_QIN = 2, SC3_QOUT = 3, SC3_UMEAN = 4, SC3_N = 8 };
 
@@ -64,6 +66,7 @@ struct D3Args {
     S* fo;                     // [slots][2][19] outlet post-boundary populations of the previous step
     S* fface;                  // [slots][2][19] post-boundary populations of this step
     S* unbr;                   // [slots][3] u^eq of the outlet's inward neighbours (Eq. 22)
+    const S* adv;              // [3][plane] sum_e w s(x+e) e of Eq. 11 (near-solid nodes)
     double* flux;              // [slots][2] flux terms of this step
     const double* scal_in;
     double* scal_out;

@@ -59,6 +59,7 @@ struct Ctx3 {
     void* fo = nullptr;
     void* fface = nullptr;
     void* unbr = nullptr;
+    void* adv = nullptr;
     double* flux = nullptr;
     double* scal[2] = {nullptr, nullptr};
     unsigned int* status = nullptr;
@@ -68,6 +69,7 @@ struct Ctx3 {
     int64_t step = 0, launches = 0;
     std::vector<uint8_t> solid;     // [nz][ny][nx]
     std::vector<uint32_t> hinfo;    // [nz][ny][pitch]
+    std::vector<double> hadv;       // [3][nz][ny][pitch] adhesion vectors
     std::vector<double> face_speed_h, face_rho_h;
     // kernel timing
     int time_every = 0;
@@ -148,6 +150,7 @@ void fill_args(const Ctx3* c, D3Args<T>& a, bool write_u) {
     a.fo = static_cast<T*>(c->fo);
     a.fface = static_cast<T*>(c->fface);
     a.unbr = static_cast<T*>(c->unbr);
+    a.adv = static_cast<const T*>(c->adv);
     a.flux = c->flux;
     a.scal_in = c->scal[c->step & 1];
     a.scal_out = c->scal[(c->step + 1) & 1];
@@ -168,7 +171,10 @@ lbm_status upload_state(Ctx3* c, const double* rho_init, const double* u_init) {
         for (int y = 0; y < c->ny; ++y)
             for (int x = 0; x < c->nx; ++x) {
                 const long long h = hidx(c, x, y, z), d = didx(c, x, y, z);
-                if (c->solid[h]) continue;
+                if (c->solid[h]) {
+                    rh[d] = T(SOLID_MARK);  // solid marker of the density field (psi = 0 there)
+                    continue;
+                }
                 double u[3];
                 for (int a = 0; a < 3; ++a) u[a] = u_init ? u_init[(size_t)a * N + h] : 0.0;
                 for (int k = 0; k < 2; ++k) {
@@ -230,7 +236,7 @@ void destroy(Ctx3* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     void* p[] = {c->f[0], c->f[1], c->info, c->rho, c->umac, c->face_speed, c->face_rho, c->face_fluid, c->FpF,
-                 c->FpN, c->fo, c->fface, c->unbr, c->flux, c->scal[0], c->scal[1], c->status, c->mass_partial};
+                 c->FpN, c->fo, c->fface, c->unbr, c->adv, c->flux, c->scal[0], c->scal[1], c->status, c->mass_partial};
     for (void* q : p)
         if (q) cudaFree(q);
     for (cudaEvent_t e : c->ev)
@@ -395,6 +401,7 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
 
     // info words
     c->hinfo.assign((size_t)c->plane, INFO3_SOLID);
+    c->hadv.assign((size_t)3 * c->plane, 0.0);
     for (int z = 0; z < c->nz; ++z)
         for (int y = 0; y < c->ny; ++y)
             for (int x = 0; x < c->nx; ++x) {
@@ -420,15 +427,26 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
                 }
                 w |= (uint32_t)faceid[h] << INFO3_FACE_SHIFT;
                 w |= (uint32_t)nbrid[h] << INFO3_NBR_SHIFT;
+                // sum_e w s(x+e) e over the 8th-order stencil (Eq. 11)
+                static const int W5040[9] = {0, 448, 240, 96, 50, 16, 8, 0, 1};
+                double adh[3] = {0.0, 0.0, 0.0};
                 bool near = false;
-                for (int dz = -2; dz <= 2 && !near; ++dz)
-                    for (int dy = -2; dy <= 2 && !near; ++dy)
-                        for (int dx = -2; dx <= 2 && !near; ++dx) {
+                for (int dz = -2; dz <= 2; ++dz)
+                    for (int dy = -2; dy <= 2; ++dy)
+                        for (int dx = -2; dx <= 2; ++dx) {
                             const int r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 == 0 || r2 > 8 || r2 == 7) continue;
-                            if (host_site(c, x + dx, y + dy, z + dz) < 0) near = true;
+                            if (r2 == 0 || r2 > 8 || W5040[r2] == 0) continue;
+                            if (host_site(c, x + dx, y + dy, z + dz) >= 0) continue;
+                            near = true;
+                            const double wgt = W5040[r2] / 5040.0;
+                            adh[0] += wgt * dx;
+                            adh[1] += wgt * dy;
+                            adh[2] += wgt * dz;
                         }
-                if (near) w |= INFO3_NEAR_SOLID;
+                if (near) {
+                    w |= INFO3_NEAR_SOLID;
+                    for (int q = 0; q < 3; ++q) c->hadv[(size_t)q * c->plane + didx(c, x, y, z)] = adh[q];
+                }
                 c->hinfo[didx(c, x, y, z)] = w;
             }
 
@@ -450,6 +468,7 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
     alloc(&c->fo, (size_t)slots * 2 * Q * c->sb);
     alloc(&c->fface, (size_t)slots * 2 * Q * c->sb);
     alloc(&c->unbr, (size_t)slots * 3 * c->sb);
+    alloc(&c->adv, (size_t)3 * c->plane * c->sb);
     alloc((void**)&c->flux, (size_t)slots * 2 * sizeof(double));
     alloc((void**)&c->scal[0], SC3_N * sizeof(double));
     alloc((void**)&c->scal[1], SC3_N * sizeof(double));
@@ -463,6 +482,15 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
         return fail3(nullptr, err, st, msg);
     }
     e = cudaMemcpy(c->info, c->hinfo.data(), c->hinfo.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        if (c->sb == 8) {
+            e = cudaMemcpy(c->adv, c->hadv.data(), c->hadv.size() * sizeof(double), cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> af(c->hadv.begin(), c->hadv.end());
+            e = cudaMemcpy(c->adv, af.data(), af.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
+    }
+    std::vector<double>().swap(c->hadv);
     if (e == cudaSuccess && slots > 0) {
         e = cudaMemcpy(c->face_speed, c->face_speed_h.data(), (size_t)slots * sizeof(double), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
