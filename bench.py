@@ -28,8 +28,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 KERNEL_SRC = os.path.join(ROOT, "paper_2512_12934_gb300", "csrc", "lbm_d2q9.cu")
+KERNEL_SRC_3D = os.path.join(ROOT, "paper_2512_12934_gb300", "csrc", "lbm_d3q19.cu")
+PROFILE_SUMMARY_3D = os.path.join(ROOT, "profiles", "d3q19_step_coflow_512x96x96.md")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "d2q9_step_channel_1024x128.md")
 BYTES_PER_NODE = {"fp32": 144, "fp16store": 80, "fp64": 288}
+BYTES_PER_NODE_3D = {"fp32": 304, "fp64": 608}  # 38 populations read + written per fluid node and step
 DTYPE = {"fp32": "f32", "fp16store": "f16-storage/f32", "fp64": "f64"}
 
 
@@ -42,7 +45,7 @@ def parse():
     p.add_argument("--lbm-steps", type=int, default=5000, help="LBM time steps per benchmark step")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16store", "fp64"])
     p.add_argument("--workload", default="channel",
-                   choices=["channel", "channel_hbm", "tjunction_batch", "surrogate"],
+                   choices=["channel", "channel_hbm", "tjunction_batch", "surrogate", "coflow3d"],
                    help="channel: the 1024x128 config; channel_hbm: the same physics on 8192x2048; "
                         "tjunction_batch: the T-junction ensemble, batched vs sequential")
     p.add_argument("--instances", type=int, default=256, help="ensemble size for tjunction_batch")
@@ -54,6 +57,10 @@ def parse():
     p.add_argument("--sur-train", type=int, default=1024, help="solver runs used to train the surrogate")
     p.add_argument("--sur-test", type=int, default=256, help="held-out solver runs judging the surrogate")
     p.add_argument("--no-mlp", action="store_true", help="skip the surrogate-kernel entry of the default line")
+    p.add_argument("--no-3d", action="store_true", help="skip the D3Q19 co-flow entry of the default line")
+    p.add_argument("--hbm-nx", type=int, default=8192, help="x extent of the HBM-resident channel grid")
+    p.add_argument("--hbm-ny", type=int, default=2048, help="y extent of the HBM-resident channel grid")
+    p.add_argument("--lbm-steps-3d", type=int, default=200, help="D3Q19 time steps per benchmark step")
     return p.parse_args()
 
 
@@ -138,6 +145,20 @@ def profiled_traffic():
     return float(m_traffic.group(1))
 
 
+def profiled_traffic_3d():
+    """DRAM bytes of one D3Q19 co-flow step from the committed ncu summary, if
+    it was taken on the current kernel source; else None."""
+    if not os.path.exists(PROFILE_SUMMARY_3D):
+        return None
+    text = open(PROFILE_SUMMARY_3D).read()
+    h = hashlib.sha256(open(KERNEL_SRC_3D, "rb").read()).hexdigest()[:16]
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_traffic = re.search(r"dram_bytes_per_step_full_size:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_traffic or m_hash.group(1) != h:
+        return None
+    return float(m_traffic.group(1))
+
+
 def cpu_oracle_sample(w, seconds, threads, min_steps=1):
     """Time the FP64 oracle on the host cores on the same grid; returns MLUPS."""
     from oracle import oracle as O
@@ -211,6 +232,74 @@ MLP_FWD_FLOP = 2 * (4 * 128 + 2 * 128 * 128 + 128 * 2)
 MLP_BWD_FLOP = 4 * 2 * 128 + 8 * 128 * 128 + 2 * 128 * 4
 # FP32 FMA peak of the SIMT pipes: 152 SMs x 128 lanes x 2 FLOP at 2070 MHz.
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def coflow3d(precision, stream_handle, bench_steps, lbm_steps, warmup, e2e=True):
+    """The 512x96x96 coaxial co-flow device on the D3Q19 path: device-timed
+    MLUPS over bench_steps x lbm_steps time steps (CUDA events), the sampled
+    split between the pull and collide phases, and the step roofline."""
+    import numpy as np
+    import torch
+
+    from paper_2512_12934_gb300 import lbm
+    from paper_2512_12934_gb300 import workloads as W
+
+    w = W.coflow3()
+    s = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision=precision, stream=stream_handle)
+    try:
+        for _ in range(warmup):
+            s.step(lbm_steps)
+        s.sync()
+        s.enable_kernel_timing(17)
+        launches0 = s.diagnostics()["launches"]
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        ev0.record(st)
+        for _ in range(bench_steps):
+            s.step(lbm_steps)
+        ev1.record(st)
+        torch.cuda.synchronize()
+        elapsed = ev0.elapsed_time(ev1) / 1e3
+        pull_ms, collide_ms, nsamp = s.kernel_time_split()
+        d = s.diagnostics()
+        launches = d["launches"] - launches0 - 1
+        e2e_res = None
+        if e2e:
+            rho_h = np.ascontiguousarray(w.rho, dtype=np.float64)
+            u_h = np.ascontiguousarray(w.u, dtype=np.float64)
+            out_r = np.empty((2,) + w.rho.shape[1:], dtype=np.float32)
+            out_u = np.empty((3,) + w.rho.shape[1:], dtype=np.float32)
+            s.enable_kernel_timing(0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.reset(rho_h, u_h)                       # H2D: populations, fields, open-face state
+            s.step(lbm_steps)
+            s.macros_f32(out_r.ctypes.data, out_u.ctypes.data, device=False)  # D2H
+            el = time.perf_counter() - t0
+            nodes = w.cfg["nx"] * w.cfg["ny"] * w.cfg["nz"]
+            e2e_res = {"value": w.fluid_nodes * lbm_steps / el / 1e6, "unit": "MLUPS",
+                       "h2d_bytes_per_step": nodes * 8 * (2 + 3), "d2h_bytes_per_step": nodes * 4 * 5,
+                       "api": "lbm_reset(host fields) + lbm_step + lbm_get_macros(host)"}
+    finally:
+        s.close()
+    nsteps = bench_steps * lbm_steps
+    step_s = elapsed / nsteps
+    bpn = BYTES_PER_NODE_3D[precision]
+    achieved = bpn * w.fluid_nodes / step_s / 1e9
+    peak, kind = measured_peaks()
+    return {"workload": "coflow3d_512x96x96", "fluid_nodes": w.fluid_nodes, "lbm_steps": nsteps,
+            "mlups": w.fluid_nodes / step_s / 1e6, "ms_per_lbm_step": step_s * 1e3,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic_3d(),
+                         "kernel": "one D3Q19 step (pull + face + collide + outlet + reduce kernels)",
+                         "algorithmic_bytes_per_launch": bpn * w.fluid_nodes,
+                         "peak_source": "%s hbm_gbs (copy, burst)" % kind},
+            "sampled_pull_ms": pull_ms, "sampled_collide_ms": collide_ms, "kernel_samples": nsamp,
+            "gpu_launches": launches, "e2e": e2e_res, "status": d["status"],
+            "config": {"G12": w.cfg["G12"], "Gw": list(w.cfg["Gw"]), "nu": list(w.cfg["nu"]),
+                       "r_in": w.meta["r_in"], "r_out": w.meta["r_out"], "q_ratio": w.meta["q_ratio"],
+                       "M": w.meta["M"], "u_c": w.meta["u_c"]}}
 
 
 def surrogate_cpu_baseline(solver_s_per_point, n=4096, members=5):
@@ -416,6 +505,39 @@ def main():
                                          "lbm_steps_per_step": args.lbm_steps, "precision": args.precision},
                               "batched_ensemble": res, "clocks": clk}))
         return 0
+    if args.workload == "coflow3d":
+        prec = args.precision if args.precision in BYTES_PER_NODE_3D else "fp32"
+        ck = Clocks(local)
+        ck.start()
+        barrier()
+        res = coflow3d(prec, stream.cuda_stream, args.steps, args.lbm_steps_3d, args.warmup, e2e=not args.no_e2e)
+        barrier()
+        clk = ck.stop()
+        cpu = None
+        if rank == 0 and not args.no_cpu:
+            from oracle import oracle3d as O3
+            w3 = W.coflow3()
+            threads = os.cpu_count() or 1
+            o = O3.Oracle3D(w3.cfg, w3.solid, w3.rho, w3.u, threads=threads)
+            t0 = time.perf_counter()
+            o.step(1)
+            el = time.perf_counter() - t0
+            cpu = {"value": w3.fluid_nodes / el / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                   "sample": "1 full-grid FP64 D3Q19 oracle step of the 512x96x96 co-flow, %.1f s, %d threads" % (
+                       el, threads)}
+        if rank == 0:
+            print(json.dumps({
+                "metric": "MLUPS", "value": res["mlups"] * world, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_lbm_step"] * args.lbm_steps_3d,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec],
+                "data": "synthetic",
+                "config": {"workload": res["workload"], "grid": [512, 96, 96], "fluid_nodes": res["fluid_nodes"],
+                           "lbm_steps_per_step": args.lbm_steps_3d, "precision": prec,
+                           "l2": "state (1.4 GB) far larger than L2", **res["config"]},
+                "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": res["e2e"],
+                "gpu_launches": res["gpu_launches"], "clocks": clk, "status": res["status"],
+                "sampled_pull_ms": res["sampled_pull_ms"], "sampled_collide_ms": res["sampled_collide_ms"]}))
+        return 0
     if args.workload == "surrogate":
         ck = Clocks(local)
         ck.start()
@@ -444,7 +566,7 @@ def main():
                         "api": "Surrogate.predict(host points) -> lbm_mlp_predict(host arrays)"},
                 "cpu_baseline": cpu, "gpu_launches": 2 * 10, "clocks": clk}))
         return 0
-    w = W.channel() if args.workload == "channel" else W.channel(nx=8192, ny=2048, R=240, xc=1600)
+    w = W.channel() if args.workload == "channel" else W.channel(nx=args.hbm_nx, ny=args.hbm_ny, R=240, xc=1600)
     S = args.lbm_steps
     solver = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision=args.precision, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -506,7 +628,7 @@ def main():
     # ---- the same physics on an HBM-resident grid (roofline of the kernel proper)
     hbm = None
     if not args.no_hbm:
-        big = W.channel(nx=8192, ny=2048, R=240, xc=1600)
+        big = W.channel(nx=args.hbm_nx, ny=args.hbm_ny, R=240, xc=1600)
         sb = lbm.Solver(big.cfg, big.solid, big.rho, big.u, precision=args.precision,
                         stream=stream.cuda_stream)
         sb.step(20)
@@ -519,7 +641,7 @@ def main():
         bach = bpn * fast_nodes / (bfast / 1e3) / 1e9
         hbm = {"bound": "hbm", "achieved": bach, "peak": peak, "unit": "GB/s", "frac": bach / peak,
                "kernel": "d2q9_step_kernel fast tile list", "kernel_ms": bfast,
-               "general_list_ms": bgen, "kernel_samples": bn, "grid": [8192, 2048],
+               "general_list_ms": bgen, "kernel_samples": bn, "grid": [args.hbm_nx, args.hbm_ny],
                "algorithmic_bytes_per_launch": bpn * fast_nodes,
                "mlups_step": big.fluid_nodes / ((bfast + bgen) / 1e3) / 1e6}
         del big
@@ -562,6 +684,9 @@ def main():
     mlp = None
     if not args.no_mlp and args.workload == "channel":
         mlp = mlp_kernels(stream.cuda_stream)
+    d3 = None
+    if not args.no_3d and args.workload == "channel":
+        d3 = coflow3d("fp32", stream.cuda_stream, 2, 100, 1, e2e=False)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -587,6 +712,7 @@ def main():
             "roofline_hbm_resident": hbm,
             "batched_ensemble": batched,
             "surrogate_kernels": mlp,
+            "d3q19_coflow": d3,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
