@@ -352,7 +352,7 @@ def duct3(nx=24, ny=10, nz=9, R=3.0, xc=8.0, u_max=0.01, G12=1.6, Gw=(0.2, -0.2)
     return Workload("duct3_%dx%dx%d" % (nx, ny, nz), cfg, solid, rho, u, 0, {"u_max": u_max})
 
 
-def coflow3(nx=512, ny=96, nz=96, r_in=12, wall=2, r_out=46, nozzle=48, q_ratio=0.5, M=0.2, G12=1.6,
+def coflow3(nx=512, ny=96, nz=96, r_in=12, wall=2, r_out=46, nozzle=48, q_ratio=0.5, M=0.2, G12=1.2,
             Gw=(0.2, -0.2), u_c=0.01, nu_c=1.0 / 6) -> Workload:
     """Coaxial co-flow droplet generator (Sec. III D, Fig. 10): a tube of
     radius r_out along x; a nozzle (solid shell r_in < r <= r_in + wall)
@@ -362,7 +362,11 @@ def coflow3(nx=512, ny=96, nz=96, r_in=12, wall=2, r_out=46, nozzle=48, q_ratio=
     and composition), one convective outlet covers x = nx-1.  Pipe-flow
     profiles: Poiseuille in the bore, the annular Poiseuille profile in the
     annulus, scaled so the dispersed/continuous flow-rate ratio is q_ratio
-    and the continuous peak speed is u_c."""
+    and the continuous peak speed is u_c.  G12 defaults to 1.2: with the
+    derived 3D interaction weights this device diverges within 250 steps at
+    G12 >= 2.0 and within ~1000 steps at 1.6 (with wall adhesion), and stays
+    finite for >= 3000 steps at 1.2 over M in {0.2, 1}, u_c in {0.005, 0.01}
+    and G_w in {0, 0.2}."""
     cy, cz = (ny - 1) / 2.0, (nz - 1) / 2.0
     z, y = np.mgrid[0:nz, 0:ny].astype(np.float64)
     r = np.sqrt((y - cy) ** 2 + (z - cz) ** 2)
