@@ -694,19 +694,25 @@ __global__ void __launch_bounds__(128) d3q_outlet_kernel(D3Args<S> a) {
 }
 
 // ---- kernel C: lambda and chi from the face flux terms (fixed order) -------
+// One block of 1024 threads; each thread owns a fixed set of slots and the
+// tree below has a fixed shape, so the sums are deterministic.  Slots of
+// solid face positions hold the zeros they were created with.
+constexpr int RED = 1024;
 template <typename S>
-__global__ void __launch_bounds__(256) d3q_reduce_kernel(D3Args<S> a) {
-    __shared__ double s_in[256], s_out[256], s_u[256];
+__global__ void __launch_bounds__(RED) d3q_reduce_kernel(D3Args<S> a) {
+    __shared__ double s_in[RED], s_out[RED], s_u[RED];
     double qin = 0.0, qout = 0.0, us = 0.0;
+    const double2* fl = reinterpret_cast<const double2*>(a.flux);
     for (int f = 0; f < a.nfaces; ++f) {
         const FaceDev3& F = a.face[f];
-        for (int q = threadIdx.x; q < F.count; q += 256) {
-            const int slot = F.base + q;
-            if (!a.face_fluid[slot]) continue;
-            if (F.kind == FACE3_INLET) qin += a.flux[(size_t)slot * 2];
+        const bool inlet = F.kind == FACE3_INLET;
+#pragma unroll 4
+        for (int q = threadIdx.x; q < F.count; q += RED) {
+            const double2 v = fl[F.base + q];
+            if (inlet) qin += v.x;
             else {
-                qout += a.flux[(size_t)slot * 2];
-                us += a.flux[(size_t)slot * 2 + 1];
+                qout += v.x;
+                us += v.y;
             }
         }
     }
@@ -714,7 +720,7 @@ __global__ void __launch_bounds__(256) d3q_reduce_kernel(D3Args<S> a) {
     s_out[threadIdx.x] = qout;
     s_u[threadIdx.x] = us;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
+    for (int w = RED / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) {
             s_in[threadIdx.x] += s_in[threadIdx.x + w];
             s_out[threadIdx.x] += s_out[threadIdx.x + w];
@@ -800,7 +806,7 @@ cudaError_t launch_step(const D3Args<S>& a, cudaStream_t st, cudaEvent_t mid_a, 
     if (a.nface_slots > 0) {
         d3q_outlet_kernel<S><<<fblocks, 128, 0, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        d3q_reduce_kernel<S><<<1, 256, 0, st>>>(a);
+        d3q_reduce_kernel<S><<<1, RED, 0, st>>>(a);
         e = cudaGetLastError();
     }
     return e;
