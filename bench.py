@@ -32,7 +32,7 @@ KERNEL_SRC_3D = os.path.join(ROOT, "paper_2512_12934_gb300", "csrc", "lbm_d3q19.
 PROFILE_SUMMARY_3D = os.path.join(ROOT, "profiles", "d3q19_step_coflow_512x96x96.md")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "d2q9_step_channel_1024x128.md")
 BYTES_PER_NODE = {"fp32": 144, "fp16store": 80, "fp64": 288}
-BYTES_PER_NODE_3D = {"fp32": 304, "fp64": 608}  # 38 populations read + written per fluid node and step
+BYTES_PER_NODE_3D = {"fp32": 304, "fp16store": 160, "fp64": 608}  # 38 populations read + written per node and step (+ 2 half references read + written for fp16store)
 DTYPE = {"fp32": "f32", "fp16store": "f16-storage/f32", "fp64": "f64"}
 
 

@@ -136,6 +136,25 @@ template <>
 struct Store<double> {
     using R = double;
 };
+template <>
+struct Store<__half> {
+    using R = float;
+};
+
+template <typename S>
+__device__ __forceinline__ constexpr bool is_half() {
+    return std::is_same<S, __half>::value;
+}
+
+// A stored population as a real number (FP16 storage: the deviation only).
+template <typename S>
+__device__ __forceinline__ typename Store<S>::R ld_pop(S v) {
+    if constexpr (is_half<S>()) return __half2float(v);
+    else return v;
+}
+
+// Density rounded to the half-precision reference of FP16 storage.
+__device__ __forceinline__ float half_round(float r) { return __half2float(__float2half_rn(r)); }
 
 // Wrap a pull source on periodic axes (blocked sources never reach here).
 __device__ __forceinline__ int wrap(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
@@ -154,10 +173,14 @@ __device__ __forceinline__ void pull(const D3Args<S>& a, int k, int x, int y, in
     const long long n = node_index(a, x, y, z);
     const long long sy = a.pitch, sz = (long long)a.ny * a.pitch;
     const bool wrapped = (info & INFO3_WRAP) != 0;
+    // FP16 storage: every value this node pulls was encoded against its
+    // reference density (the writer used the same half-rounded density)
+    R ref = 0;
+    if constexpr (is_half<S>()) ref = __half2float(a.rref_in[(size_t)k * a.plane + n]);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         if (info & (1u << i)) {
-            f[i] = (R)fin[(size_t)opp_(i) * a.plane + n];
+            f[i] = (R)ld_pop(fin[(size_t)opp_(i) * a.plane + n]);
         } else if (!wrapped) {
             long long src = n;
             if constexpr (ex_(i) != 0) src -= ex_(i);
@@ -165,13 +188,14 @@ __device__ __forceinline__ void pull(const D3Args<S>& a, int k, int x, int y, in
             if constexpr (ey_(i) == -1) src += sy;
             if constexpr (ez_(i) == 1) src -= sz;
             if constexpr (ez_(i) == -1) src += sz;
-            f[i] = (R)fin[(size_t)i * a.plane + src];
+            f[i] = (R)ld_pop(fin[(size_t)i * a.plane + src]);
         } else {
             const int xs = ex_(i) ? wrap(x - ex_(i), a.nx) : x;
             const int ys = ey_(i) ? wrap(y - ey_(i), a.ny) : y;
             const int zs = ez_(i) ? wrap(z - ez_(i), a.nz) : z;
-            f[i] = (R)fin[(size_t)i * a.plane + node_index(a, xs, ys, zs)];
+            f[i] = (R)ld_pop(fin[(size_t)i * a.plane + node_index(a, xs, ys, zs)]);
         }
+        if constexpr (is_half<S>()) f[i] += ((R)w36_(i) / (R)36) * ref;
     });
 }
 
@@ -519,11 +543,23 @@ __device__ __forceinline__ void add_j(const R (&f)[Q], R (&j)[3]) {
     j[2] += jz;
 }
 
-template <typename S>
-__device__ __forceinline__ void store_pop(const D3Args<S>& a, int k, long long n, const typename Store<S>::R (&f)[Q]) {
+// Store the post-collision populations of component k at node n.  FP16
+// storage writes half(f*_i - w_i rho_ref), rho_ref being the half-rounded
+// density of component k at the node that pulls f*_i next step: x + e_i, or
+// x itself when that neighbour is solid or outside (halfway bounce-back).
+// dest_rho(I, k) returns that density.
+template <typename S, typename DestRho>
+__device__ __forceinline__ void store_pop(const D3Args<S>& a, int k, long long n, const typename Store<S>::R (&f)[Q],
+                                          DestRho dest_rho) {
+    using R = typename Store<S>::R;
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        a.fout[(size_t)(k * Q + i) * a.plane + n] = (S)f[i];
+        if constexpr (is_half<S>()) {
+            const R ref = half_round(dest_rho(I, k));
+            a.fout[(size_t)(k * Q + i) * a.plane + n] = __float2half_rn(f[i] - ((R)w36_(i) / (R)36) * ref);
+        } else {
+            a.fout[(size_t)(k * Q + i) * a.plane + n] = (S)f[i];
+        }
     });
 }
 
@@ -638,9 +674,21 @@ __global__ void __launch_bounds__(256) d3q_collide_kernel(D3Args<S> a) {
         a.flux[(size_t)slot * 2 + 1] = 0.0;
     }
     check_store_u<S>(a, n, rt, u);
+    // reader densities for FP16 storage: the staged tile (periodic wraps
+    // resolved) or this node when the direction is blocked
+    auto dest_rho = [&](auto I, int k) -> R {
+        constexpr int i = decltype(I)::value;
+        const int h = (info & (1u << opp_(i))) ? hc : hc + ex_(i) + HX * (ey_(i) + HY * ez_(i));
+        const typename Pair<R>::type v = s_rr[h];
+        return k ? v.y : v.x;
+    };
+    if constexpr (is_half<S>()) {
+        a.rref_out[n] = __float2half_rn(r1);
+        a.rref_out[a.plane + n] = __float2half_rn(r2);
+    }
     // collide component 1 (still in registers), then reload component 0
     collide<R>(f, r2, u[0], u[1], u[2], F2[0], F2[1], F2[2], a.s[1]);
-    store_pop<S>(a, 1, n, f);
+    store_pop<S>(a, 1, n, f, dest_rho);
     if (fid == 0) {
         pull<S, R>(a, 0, x, y, z, info, f);
     } else {
@@ -651,7 +699,7 @@ __global__ void __launch_bounds__(256) d3q_collide_kernel(D3Args<S> a) {
         });
     }
     collide<R>(f, r1, u[0], u[1], u[2], F1[0], F1[1], F1[2], a.s[0]);
-    store_pop<S>(a, 0, n, f);
+    store_pop<S>(a, 0, n, f, dest_rho);
 }
 
 // One thread per outlet slot: the outlet node's velocity with the normal
@@ -683,14 +731,25 @@ __global__ void __launch_bounds__(128) d3q_outlet_kernel(D3Args<S> a) {
     for (int q = 0; q < 3; ++q) u[q] = (j[q] + (R)0.5 * (F1[q] + F2[q])) / rt;
     if (Fc.chi) u[Fc.axis] = (R)a.scal_in[SC3_CHI] * a.unbr[(size_t)slot * 3 + Fc.axis];
     check_store_u<S>(a, n, rt, u);
+    const uint32_t info = a.info[n];
+    auto dest_rho = [&](auto I, int k) -> R {
+        constexpr int i = decltype(I)::value;
+        long long m = n;
+        if (!(info & (1u << opp_(i)))) m = site_index(a, c[0] + ex_(i), c[1] + ey_(i), c[2] + ez_(i));
+        return a.rho[(size_t)k * a.plane + m];
+    };
+    if constexpr (is_half<S>()) {
+        a.rref_out[n] = __float2half_rn(r1);
+        a.rref_out[a.plane + n] = __float2half_rn(r2);
+    }
     collide<R>(f, r2, u[0], u[1], u[2], F2[0], F2[1], F2[2], a.s[1]);
-    store_pop<S>(a, 1, n, f);
+    store_pop<S>(a, 1, n, f, dest_rho);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         f[i] = ff[i];
     });
     collide<R>(f, r1, u[0], u[1], u[2], F1[0], F1[1], F1[2], a.s[0]);
-    store_pop<S>(a, 0, n, f);
+    store_pop<S>(a, 0, n, f, dest_rho);
 }
 
 // ---- kernel C: lambda and chi from the face flux terms (fixed order) -------
@@ -749,7 +808,8 @@ __global__ void __launch_bounds__(RED) d3q_reduce_kernel(D3Args<S> a) {
 // ---- diagnostics: FP64 masses over fluid nodes and the largest |u|^2 ------
 template <typename S>
 __global__ void __launch_bounds__(256) d3q_mass_kernel(const S* __restrict__ f, const uint32_t* __restrict__ info,
-                                                       const S* __restrict__ umac, int nx, int ny, int nz,
+                                                       const typename Store<S>::R* __restrict__ umac,
+                                                       const __half* __restrict__ rref, int nx, int ny, int nz,
                                                        int pitch, long long plane, double* __restrict__ partial) {
     __shared__ double s0[256], s1[256], s2[256];
     double m0 = 0.0, m1 = 0.0, u2 = 0.0;
@@ -757,12 +817,30 @@ __global__ void __launch_bounds__(256) d3q_mass_kernel(const S* __restrict__ f, 
     for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < total; q += (long long)gridDim.x * 256) {
         const int x = (int)(q % nx);
         const long long yz = q / nx;
+        const int y = (int)(yz % ny), z = (int)(yz / ny);
         const long long n = yz * pitch + x;
-        if (info[n] & INFO3_SOLID) continue;
-        for (int i = 0; i < Q; ++i) {
-            m0 += (double)f[(size_t)i * plane + n];
-            m1 += (double)f[(size_t)(Q + i) * plane + n];
-        }
+        const uint32_t inf = info[n];
+        if (inf & INFO3_SOLID) continue;
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            double v0 = (double)ld_pop(f[(size_t)i * plane + n]);
+            double v1 = (double)ld_pop(f[(size_t)(Q + i) * plane + n]);
+            if constexpr (is_half<S>()) {
+                // decode with the reference of the node that will pull the value
+                long long m = n;
+                if (!(inf & (1u << opp_(i)))) {
+                    const int xs = ex_(i) ? wrap(x + ex_(i), nx) : x;
+                    const int ys = ey_(i) ? wrap(y + ey_(i), ny) : y;
+                    const int zs = ez_(i) ? wrap(z + ez_(i), nz) : z;
+                    m = ((long long)zs * ny + ys) * pitch + xs;
+                }
+                const double w = (double)w36_(i) / 36.0;
+                v0 += w * (double)__half2float(rref[m]);
+                v1 += w * (double)__half2float(rref[plane + m]);
+            }
+            m0 += v0;
+            m1 += v1;
+        });
         const double ux = (double)umac[n], uy = (double)umac[plane + n], uz = (double)umac[2 * plane + n];
         u2 = fmax(u2, ux * ux + uy * uy + uz * uz);
     }
@@ -813,17 +891,21 @@ cudaError_t launch_step(const D3Args<S>& a, cudaStream_t st, cudaEvent_t mid_a, 
 }
 
 template <typename S>
-cudaError_t launch_mass(const S* f, const uint32_t* info, const S* umac, int nx, int ny, int nz, int pitch,
-                        long long plane, double* partial, int nblocks, cudaStream_t st) {
-    d3q_mass_kernel<S><<<nblocks, 256, 0, st>>>(f, info, umac, nx, ny, nz, pitch, plane, partial);
+cudaError_t launch_mass(const S* f, const uint32_t* info, const typename Real<S>::type* umac, const __half* rref,
+                        int nx, int ny, int nz, int pitch, long long plane, double* partial, int nblocks,
+                        cudaStream_t st) {
+    d3q_mass_kernel<S><<<nblocks, 256, 0, st>>>(f, info, umac, rref, nx, ny, nz, pitch, plane, partial);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_step<float>(const D3Args<float>&, cudaStream_t, cudaEvent_t, cudaEvent_t);
 template cudaError_t launch_step<double>(const D3Args<double>&, cudaStream_t, cudaEvent_t, cudaEvent_t);
-template cudaError_t launch_mass<float>(const float*, const uint32_t*, const float*, int, int, int, int, long long,
-                                        double*, int, cudaStream_t);
-template cudaError_t launch_mass<double>(const double*, const uint32_t*, const double*, int, int, int, int,
-                                         long long, double*, int, cudaStream_t);
+template cudaError_t launch_step<__half>(const D3Args<__half>&, cudaStream_t, cudaEvent_t, cudaEvent_t);
+template cudaError_t launch_mass<float>(const float*, const uint32_t*, const float*, const __half*, int, int, int,
+                                        int, long long, double*, int, cudaStream_t);
+template cudaError_t launch_mass<double>(const double*, const uint32_t*, const double*, const __half*, int, int, int,
+                                         int, long long, double*, int, cudaStream_t);
+template cudaError_t launch_mass<__half>(const __half*, const uint32_t*, const float*, const __half*, int, int, int,
+                                         int, long long, double*, int, cudaStream_t);
 
 }  // namespace lbm3

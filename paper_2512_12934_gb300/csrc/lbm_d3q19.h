@@ -1,6 +1,7 @@
 // D3Q19 kernels: argument block, face descriptors and launchers.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -44,8 +45,21 @@ __host__ __device__ inline int face_slot(const FaceDev3& F, int x, int y, int z)
     return F.base + (c[F.a1] - F.lo1) * F.len0 + (c[F.a0] - F.lo0);
 }
 
+// Arithmetic type of a storage type: FP16 storage computes in float.
+template <typename S>
+struct Real {
+    using type = S;
+};
+template <>
+struct Real<__half> {
+    using type = float;
+};
+
+// Kernel arguments.  S is the population storage type; densities,
+// velocities and every per-face-slot array are kept in R = Real<S>::type.
 template <typename S>
 struct D3Args {
+    using R = typename Real<S>::type;
     int nx, ny, nz, pitch;
     long long plane;
     int periodic[3];
@@ -53,27 +67,32 @@ struct D3Args {
     const S* fin;
     S* fout;
     const uint32_t* info;
-    S* rho;   // [2][plane] component densities of the step
-    S* umac;  // [3][plane] u^eq of the step (may be null)
+    R* rho;   // [2][plane] component densities of the step
+    R* umac;  // [3][plane] u^eq of the step (may be null)
+    // FP16 storage only: [2][plane] half-rounded density of each node, the
+    // reference its pulled populations are decoded with (in: this step's
+    // populations, out: the ones this step writes)
+    const __half* rref_in;
+    __half* rref_out;
     int nfaces;
     FaceDev3 face[6];
     int nface_slots, have_inlet, out_count;
     const double* face_speed;  // [slots] inward normal speed
     const double* face_rho;    // [2][slots] inlet composition
     const uint8_t* face_fluid; // [slots]
-    S* FpF;                    // [slots][2][3] force at the face node (previous step)
-    S* FpN;                    // [slots][2][3] force at its inward neighbour
-    S* fo;                     // [slots][2][19] outlet post-boundary populations of the previous step
-    S* fface;                  // [slots][2][19] post-boundary populations of this step
-    S* unbr;                   // [slots][3] u^eq of the outlet's inward neighbours (Eq. 22)
-    const S* adv;              // [3][plane] sum_e w s(x+e) e of Eq. 11 (near-solid nodes)
+    R* FpF;                    // [slots][2][3] force at the face node (previous step)
+    R* FpN;                    // [slots][2][3] force at its inward neighbour
+    R* fo;                     // [slots][2][19] outlet post-boundary populations of the previous step
+    R* fface;                  // [slots][2][19] post-boundary populations of this step
+    R* unbr;                   // [slots][3] u^eq of the outlet's inward neighbours (Eq. 22)
+    const R* adv;              // [3][plane] sum_e w s(x+e) e of Eq. 11 (near-solid nodes)
     double* flux;              // [slots][2] flux terms of this step
     const double* scal_in;
     double* scal_out;
     unsigned int* status;
-    S G[3];  // G12, G_w,1, G_w,2
-    S body[3];
-    S s[2][Q];
+    R G[3];  // G12, G_w,1, G_w,2
+    R body[3];
+    R s[2][Q];
 };
 
 template <typename S>
@@ -81,9 +100,11 @@ cudaError_t launch_step(const D3Args<S>& a, cudaStream_t st, cudaEvent_t mid_a =
                         cudaEvent_t mid_b = nullptr);
 
 // FP64 sums over fluid nodes of each component's populations and the
-// largest |u|^2: partial [nblocks][3].
+// largest |u|^2: partial [nblocks][3].  FP16 storage decodes every
+// population with the reference density of the node that reads it (rref).
 template <typename S>
-cudaError_t launch_mass(const S* f, const uint32_t* info, const S* umac, int nx, int ny, int nz, int pitch,
-                        long long plane, double* partial, int nblocks, cudaStream_t st);
+cudaError_t launch_mass(const S* f, const uint32_t* info, const typename Real<S>::type* umac, const __half* rref,
+                        int nx, int ny, int nz, int pitch, long long plane, double* partial, int nblocks,
+                        cudaStream_t st);
 
 }  // namespace lbm3

@@ -1,9 +1,11 @@
 // Host runtime of the D3Q19 path: validation, geometry classification,
 // device state, stepping and the read-back entry points.  lbm_api.cu
 // dispatches every lbm_* call on a D3Q19 context here.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -33,13 +35,38 @@ double host_feq(int i, double rho, double ux, double uy, double uz) {
     return rho * hw(i) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
 }
 
+int hopp(int i) {
+    for (int j = 0; j < Q; ++j)
+        if (HX_[j] == -HX_[i] && HY_[j] == -HY_[i] && HZ_[j] == -HZ_[i]) return j;
+    return 0;
+}
+
+// stored value <-> real value (FP16 storage: deviation from wr = w_i rho_ref)
+template <typename S>
+S enc(double v, double wr) {
+    return (S)v;
+}
+template <>
+__half enc<__half>(double v, double wr) {
+    return __float2half_rn((float)(v - wr));
+}
+template <typename S>
+double dec(S v, double wr) {
+    return (double)v;
+}
+template <>
+double dec<__half>(__half v, double wr) {
+    return (double)__half2float(v) + wr;
+}
+
 }  // namespace
 
 struct Ctx3 {
     int nx = 0, ny = 0, nz = 0, pitch = 0;
     long long plane = 0;
     int precision = LBM_FP32;
-    size_t sb = 4;  // bytes per stored value
+    size_t sb = 4;  // bytes per stored population
+    size_t rb = 4;  // bytes per real value (densities, velocities, face state)
     cudaStream_t stream = nullptr;
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
@@ -60,6 +87,7 @@ struct Ctx3 {
     void* fface = nullptr;
     void* unbr = nullptr;
     void* adv = nullptr;
+    __half* rref[2] = {nullptr, nullptr};  // FP16 storage: [2][plane] reference densities per parity
     double* flux = nullptr;
     double* scal[2] = {nullptr, nullptr};
     unsigned int* status = nullptr;
@@ -122,8 +150,87 @@ long long host_site(const Ctx3* c, int x, int y, int z) {
     return c->solid[h] ? -1 : h;
 }
 
-template <typename T>
-void fill_args(const Ctx3* c, D3Args<T>& a, bool write_u) {
+// Node (pitched index) that pulls population i of node (x, y, z) next step:
+// the neighbour x + e_i (periodic wrap), or the node itself when its pull of
+// the opposite direction is blocked (bounce-back / open-face unknown).
+long long reader_of(const Ctx3* c, int x, int y, int z, int i) {
+    const long long d = didx(c, x, y, z);
+    if (c->hinfo[d] & (1u << hopp(i))) return d;
+    int p[3] = {x + HX_[i], y + HY_[i], z + HZ_[i]};
+    const int ext[3] = {c->nx, c->ny, c->nz};
+    for (int a = 0; a < 3; ++a) p[a] = (p[a] + ext[a]) % ext[a];
+    return didx(c, p[0], p[1], p[2]);
+}
+
+// Upload populations fd [2][19][plane] (real values) into buffer `which`.
+// FP16 storage also sets that parity's reference densities to the
+// half-rounded sums of each node's populations and encodes every value
+// against the reference of the node that pulls it.
+template <typename S>
+lbm_status put_f(Ctx3* c, const std::vector<double>& fd, int which) {
+    std::vector<S> buf((size_t)2 * Q * c->plane, enc<S>(0.0, 0.0));
+    std::vector<__half> ref;
+    const bool half = std::is_same<S, __half>::value;
+    if (half) {
+        ref.assign((size_t)2 * c->plane, __float2half_rn(0.0f));
+        for (long long d = 0; d < c->plane; ++d) {
+            if (c->hinfo[d] & INFO3_SOLID) continue;
+            for (int k = 0; k < 2; ++k) {
+                double r = 0.0;
+                for (int i = 0; i < Q; ++i) r += fd[((size_t)k * Q + i) * c->plane + d];
+                ref[(size_t)k * c->plane + d] = __float2half_rn((float)r);
+            }
+        }
+    }
+    for (int z = 0; z < c->nz; ++z)
+        for (int y = 0; y < c->ny; ++y)
+            for (int x = 0; x < c->nx; ++x) {
+                const long long d = didx(c, x, y, z);
+                if (c->hinfo[d] & INFO3_SOLID) continue;
+                for (int k = 0; k < 2; ++k)
+                    for (int i = 0; i < Q; ++i) {
+                        double wr = 0.0;
+                        if (half)
+                            wr = hw(i) * (double)__half2float(ref[(size_t)k * c->plane + reader_of(c, x, y, z, i)]);
+                        buf[((size_t)k * Q + i) * c->plane + d] = enc<S>(fd[((size_t)k * Q + i) * c->plane + d], wr);
+                    }
+            }
+    CK3(cudaMemcpy(c->f[which], buf.data(), buf.size() * sizeof(S), cudaMemcpyHostToDevice));
+    if (half) CK3(cudaMemcpy(c->rref[which], ref.data(), ref.size() * sizeof(__half), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+// Download buffer `which` as real values fd [2][19][plane].
+template <typename S>
+lbm_status get_f(Ctx3* c, std::vector<double>& fd, int which) {
+    std::vector<S> buf((size_t)2 * Q * c->plane);
+    CK3(cudaMemcpy(buf.data(), c->f[which], buf.size() * sizeof(S), cudaMemcpyDeviceToHost));
+    std::vector<__half> ref;
+    const bool half = std::is_same<S, __half>::value;
+    if (half) {
+        ref.resize((size_t)2 * c->plane);
+        CK3(cudaMemcpy(ref.data(), c->rref[which], ref.size() * sizeof(__half), cudaMemcpyDeviceToHost));
+    }
+    fd.assign((size_t)2 * Q * c->plane, 0.0);
+    for (int z = 0; z < c->nz; ++z)
+        for (int y = 0; y < c->ny; ++y)
+            for (int x = 0; x < c->nx; ++x) {
+                const long long d = didx(c, x, y, z);
+                if (c->hinfo[d] & INFO3_SOLID) continue;
+                for (int k = 0; k < 2; ++k)
+                    for (int i = 0; i < Q; ++i) {
+                        double wr = 0.0;
+                        if (half)
+                            wr = hw(i) * (double)__half2float(ref[(size_t)k * c->plane + reader_of(c, x, y, z, i)]);
+                        fd[((size_t)k * Q + i) * c->plane + d] = dec<S>(buf[((size_t)k * Q + i) * c->plane + d], wr);
+                    }
+            }
+    return LBM_OK;
+}
+
+template <typename S>
+void fill_args(const Ctx3* c, D3Args<S>& a, bool write_u) {
+    using T = typename Real<S>::type;
     std::memset(&a, 0, sizeof(a));
     a.nx = c->nx;
     a.ny = c->ny;
@@ -132,8 +239,10 @@ void fill_args(const Ctx3* c, D3Args<T>& a, bool write_u) {
     a.plane = c->plane;
     for (int q = 0; q < 3; ++q) a.periodic[q] = c->periodic[q];
     for (int q = 0; q < 6; ++q) a.open_side[q] = c->open_side[q];
-    a.fin = static_cast<const T*>(c->f[c->cur]);
-    a.fout = static_cast<T*>(c->f[1 - c->cur]);
+    a.fin = static_cast<const S*>(c->f[c->cur]);
+    a.fout = static_cast<S*>(c->f[1 - c->cur]);
+    a.rref_in = c->rref[c->cur];
+    a.rref_out = c->rref[1 - c->cur];
     a.info = c->info;
     a.rho = static_cast<T*>(c->rho);
     a.umac = write_u ? static_cast<T*>(c->umac) : nullptr;
@@ -163,10 +272,12 @@ void fill_args(const Ctx3* c, D3Args<T>& a, bool write_u) {
         for (int r = 0; r < Q; ++r) a.s[k][r] = (T)c->s[k][r];
 }
 
-template <typename T>
+template <typename S>
 lbm_status upload_state(Ctx3* c, const double* rho_init, const double* u_init) {
+    using T = typename Real<S>::type;
     const long long N = (long long)c->nx * c->ny * c->nz;
-    std::vector<T> fh((size_t)2 * Q * c->plane, T(0)), rh((size_t)2 * c->plane, T(0)), uh((size_t)3 * c->plane, T(0));
+    std::vector<double> fh((size_t)2 * Q * c->plane, 0.0);
+    std::vector<T> rh((size_t)2 * c->plane, T(0)), uh((size_t)3 * c->plane, T(0));
     for (int z = 0; z < c->nz; ++z)
         for (int y = 0; y < c->ny; ++y)
             for (int x = 0; x < c->nx; ++x) {
@@ -180,13 +291,14 @@ lbm_status upload_state(Ctx3* c, const double* rho_init, const double* u_init) {
                 for (int k = 0; k < 2; ++k) {
                     const double r = rho_init[(size_t)k * N + h];
                     rh[(size_t)k * c->plane + d] = (T)r;
-                    for (int i = 0; i < Q; ++i)
-                        fh[((size_t)k * Q + i) * c->plane + d] = (T)host_feq(i, r, u[0], u[1], u[2]);
+                    for (int i = 0; i < Q; ++i) fh[((size_t)k * Q + i) * c->plane + d] = host_feq(i, r, u[0], u[1], u[2]);
                 }
                 for (int a = 0; a < 3; ++a) uh[(size_t)a * c->plane + d] = (T)u[a];
             }
     c->cur = 0;
-    CK3(cudaMemcpyAsync(c->f[0], fh.data(), fh.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    CK3(cudaStreamSynchronize(c->stream));
+    lbm_status pst = put_f<S>(c, fh, 0);
+    if (pst != LBM_OK) return pst;
     CK3(cudaMemsetAsync(c->f[1], 0, nbytes_f(c), c->stream));
     CK3(cudaMemcpyAsync(c->rho, rh.data(), rh.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
     CK3(cudaMemcpyAsync(c->umac, uh.data(), uh.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
@@ -205,13 +317,13 @@ lbm_status upload_state(Ctx3* c, const double* rho_init, const double* u_init) {
                 const long long d = didx(c, p[0], p[1], p[2]);
                 for (int k = 0; k < 2; ++k)
                     for (int i = 0; i < Q; ++i)
-                        fo[((size_t)(F.base + q) * 2 + k) * Q + i] = fh[((size_t)k * Q + i) * c->plane + d];
+                        fo[((size_t)(F.base + q) * 2 + k) * Q + i] = (T)fh[((size_t)k * Q + i) * c->plane + d];
             }
         }
         CK3(cudaMemcpyAsync(c->fo, fo.data(), fo.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
         CK3(cudaStreamSynchronize(c->stream));
-        CK3(cudaMemsetAsync(c->FpF, 0, (size_t)c->nslots * 6 * c->sb, c->stream));
-        CK3(cudaMemsetAsync(c->FpN, 0, (size_t)c->nslots * 6 * c->sb, c->stream));
+        CK3(cudaMemsetAsync(c->FpF, 0, (size_t)c->nslots * 6 * c->rb, c->stream));
+        CK3(cudaMemsetAsync(c->FpN, 0, (size_t)c->nslots * 6 * c->rb, c->stream));
     }
     double sc[SC3_N] = {0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     CK3(cudaMemcpyAsync(c->scal[0], sc, sizeof(sc), cudaMemcpyHostToDevice, c->stream));
@@ -239,6 +351,8 @@ void destroy(Ctx3* c) {
                  c->FpN, c->fo, c->fface, c->unbr, c->adv, c->flux, c->scal[0], c->scal[1], c->status, c->mass_partial};
     for (void* q : p)
         if (q) cudaFree(q);
+    for (__half* q : c->rref)
+        if (q) cudaFree(q);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
     delete c;
@@ -254,8 +368,8 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
         return fail3(nullptr, err, LBM_ERR_INVALID_ARG, "extent: every D3Q19 axis needs >= 5 nodes");
     if ((long long)g->nx * g->ny * g->nz > (1ll << 31) - 1)
         return fail3(nullptr, err, LBM_ERR_INVALID_ARG, "extent: grid too large");
-    if (p->precision != LBM_FP32 && p->precision != LBM_FP64)
-        return fail3(nullptr, err, LBM_ERR_UNSUPPORTED, "D3Q19 supports LBM_FP32 and LBM_FP64 storage");
+    if (p->precision != LBM_FP32 && p->precision != LBM_FP64 && p->precision != LBM_FP32_FP16STORE)
+        return fail3(nullptr, err, LBM_ERR_INVALID_ARG, "unknown precision");
     if (!(p->nu[0] > 0.0) || !(p->nu[1] > 0.0)) return fail3(nullptr, err, LBM_ERR_INVALID_ARG, "viscosities must be > 0");
     if (nbc < 0 || nbc > 6 || (nbc > 0 && !bcs)) return fail3(nullptr, err, LBM_ERR_INVALID_ARG, "bad face list");
     if (!rho_init) return fail3(nullptr, err, LBM_ERR_INVALID_ARG, "rho_init is NULL");
@@ -268,7 +382,8 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
     c->pitch = (g->nx + 31) / 32 * 32;
     c->plane = (long long)c->pitch * c->ny * c->nz;
     c->precision = p->precision;
-    c->sb = p->precision == LBM_FP64 ? 8 : 4;
+    c->sb = p->precision == LBM_FP64 ? 8 : (p->precision == LBM_FP32_FP16STORE ? 2 : 4);
+    c->rb = p->precision == LBM_FP64 ? 8 : 4;
     c->stream = static_cast<cudaStream_t>(stream);
     for (int a = 0; a < 3; ++a) c->periodic[a] = g->periodic[a] ? 1 : 0;
     const long long N = (long long)c->nx * c->ny * c->nz;
@@ -458,17 +573,21 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
     alloc(&c->f[0], nbytes_f(c));
     alloc(&c->f[1], nbytes_f(c));
     alloc((void**)&c->info, (size_t)c->plane * sizeof(uint32_t));
-    alloc(&c->rho, (size_t)2 * c->plane * c->sb);
-    alloc(&c->umac, (size_t)3 * c->plane * c->sb);
+    alloc(&c->rho, (size_t)2 * c->plane * c->rb);
+    alloc(&c->umac, (size_t)3 * c->plane * c->rb);
     alloc((void**)&c->face_speed, (size_t)slots * sizeof(double));
     alloc((void**)&c->face_rho, (size_t)2 * slots * sizeof(double));
     alloc((void**)&c->face_fluid, (size_t)slots);
-    alloc(&c->FpF, (size_t)slots * 6 * c->sb);
-    alloc(&c->FpN, (size_t)slots * 6 * c->sb);
-    alloc(&c->fo, (size_t)slots * 2 * Q * c->sb);
-    alloc(&c->fface, (size_t)slots * 2 * Q * c->sb);
-    alloc(&c->unbr, (size_t)slots * 3 * c->sb);
-    alloc(&c->adv, (size_t)3 * c->plane * c->sb);
+    alloc(&c->FpF, (size_t)slots * 6 * c->rb);
+    alloc(&c->FpN, (size_t)slots * 6 * c->rb);
+    alloc(&c->fo, (size_t)slots * 2 * Q * c->rb);
+    alloc(&c->fface, (size_t)slots * 2 * Q * c->rb);
+    if (c->precision == LBM_FP32_FP16STORE) {
+        alloc((void**)&c->rref[0], (size_t)2 * c->plane * sizeof(__half));
+        alloc((void**)&c->rref[1], (size_t)2 * c->plane * sizeof(__half));
+    }
+    alloc(&c->unbr, (size_t)slots * 3 * c->rb);
+    alloc(&c->adv, (size_t)3 * c->plane * c->rb);
     alloc((void**)&c->flux, (size_t)slots * 2 * sizeof(double));
     alloc((void**)&c->scal[0], SC3_N * sizeof(double));
     alloc((void**)&c->scal[1], SC3_N * sizeof(double));
@@ -483,7 +602,7 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
     }
     e = cudaMemcpy(c->info, c->hinfo.data(), c->hinfo.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        if (c->sb == 8) {
+        if (c->rb == 8) {
             e = cudaMemcpy(c->adv, c->hadv.data(), c->hadv.size() * sizeof(double), cudaMemcpyHostToDevice);
         } else {
             std::vector<float> af(c->hadv.begin(), c->hadv.end());
@@ -504,7 +623,9 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
         destroy(c);
         return fail3(nullptr, err, LBM_ERR_CUDA, msg);
     }
-    const lbm_status st = c->sb == 8 ? upload_state<double>(c, rho_init, u_init) : upload_state<float>(c, rho_init, u_init);
+    const lbm_status st = c->sb == 8   ? upload_state<double>(c, rho_init, u_init)
+                          : c->sb == 2 ? upload_state<__half>(c, rho_init, u_init)
+                                       : upload_state<float>(c, rho_init, u_init);
     if (st != LBM_OK) {
         if (err) *err = c->err;
         destroy(c);
@@ -517,7 +638,9 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
 lbm_status reset(Ctx3* c, const double* rho_init, const double* u_init) {
     if (!rho_init) return fail3(c, nullptr, LBM_ERR_INVALID_ARG, "rho_init is NULL");
     CK3(cudaStreamSynchronize(c->stream));
-    return c->sb == 8 ? upload_state<double>(c, rho_init, u_init) : upload_state<float>(c, rho_init, u_init);
+    return c->sb == 8   ? upload_state<double>(c, rho_init, u_init)
+           : c->sb == 2 ? upload_state<__half>(c, rho_init, u_init)
+                        : upload_state<float>(c, rho_init, u_init);
 }
 
 lbm_status step(Ctx3* c, int64_t nsteps) {
@@ -530,6 +653,10 @@ lbm_status step(Ctx3* c, int64_t nsteps) {
             D3Args<double> a;
             fill_args(c, a, true);
             e = launch_step<double>(a, c->stream, timed ? c->ev[1] : nullptr, timed ? c->ev[2] : nullptr);
+        } else if (c->sb == 2) {
+            D3Args<__half> a;
+            fill_args(c, a, true);
+            e = launch_step<__half>(a, c->stream, timed ? c->ev[1] : nullptr, timed ? c->ev[2] : nullptr);
         } else {
             D3Args<float> a;
             fill_args(c, a, true);
@@ -605,51 +732,61 @@ static lbm_status macros_impl(Ctx3* c, O* rho, O* u, bool dst_dev) {
 lbm_status get_macros(Ctx3* c, float* rho, float* u, int dst_is_device) {
     lbm_status st = check_status3(c);
     if (st != LBM_OK) return st;
-    return c->sb == 8 ? macros_impl<double, float>(c, rho, u, dst_is_device != 0)
+    return c->rb == 8 ? macros_impl<double, float>(c, rho, u, dst_is_device != 0)
                       : macros_impl<float, float>(c, rho, u, dst_is_device != 0);
 }
 
 lbm_status get_macros_f64(Ctx3* c, double* rho, double* u) {
     lbm_status st = check_status3(c);
     if (st != LBM_OK) return st;
-    return c->sb == 8 ? macros_impl<double, double>(c, rho, u, false) : macros_impl<float, double>(c, rho, u, false);
+    return c->rb == 8 ? macros_impl<double, double>(c, rho, u, false) : macros_impl<float, double>(c, rho, u, false);
 }
 
-template <typename T>
+template <typename S>
 static lbm_status pops_impl(Ctx3* c, double* f, const double* fin) {
     const long long N = (long long)c->nx * c->ny * c->nz;
     CK3(cudaStreamSynchronize(c->stream));
-    std::vector<T> buf((size_t)2 * Q * c->plane, T(0));
-    if (!fin) CK3(cudaMemcpy(buf.data(), c->f[c->cur], buf.size() * sizeof(T), cudaMemcpyDeviceToHost));
+    std::vector<double> fd;
+    if (!fin) {
+        lbm_status st = get_f<S>(c, fd, c->cur);
+        if (st != LBM_OK) return st;
+    } else {
+        fd.assign((size_t)2 * Q * c->plane, 0.0);
+    }
     for (int z = 0; z < c->nz; ++z)
         for (int y = 0; y < c->ny; ++y)
             for (int x = 0; x < c->nx; ++x) {
                 const long long h = hidx(c, x, y, z), d = didx(c, x, y, z);
                 for (int q = 0; q < 2 * Q; ++q) {
-                    if (fin) buf[(size_t)q * c->plane + d] = c->solid[h] ? T(0) : (T)fin[(size_t)q * N + h];
-                    else f[(size_t)q * N + h] = c->solid[h] ? 0.0 : (double)buf[(size_t)q * c->plane + d];
+                    if (fin) fd[(size_t)q * c->plane + d] = c->solid[h] ? 0.0 : fin[(size_t)q * N + h];
+                    else f[(size_t)q * N + h] = c->solid[h] ? 0.0 : fd[(size_t)q * c->plane + d];
                 }
             }
-    if (fin) CK3(cudaMemcpy(c->f[c->cur], buf.data(), buf.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (fin) return put_f<S>(c, fd, c->cur);
     return LBM_OK;
 }
 
 lbm_status get_populations(Ctx3* c, double* f) {
-    return c->sb == 8 ? pops_impl<double>(c, f, nullptr) : pops_impl<float>(c, f, nullptr);
+    return c->sb == 8 ? pops_impl<double>(c, f, nullptr)
+                      : (c->sb == 2 ? pops_impl<__half>(c, f, nullptr) : pops_impl<float>(c, f, nullptr));
 }
 
 lbm_status set_populations(Ctx3* c, const double* f) {
-    return c->sb == 8 ? pops_impl<double>(c, nullptr, f) : pops_impl<float>(c, nullptr, f);
+    return c->sb == 8 ? pops_impl<double>(c, nullptr, f)
+                      : (c->sb == 2 ? pops_impl<__half>(c, nullptr, f) : pops_impl<float>(c, nullptr, f));
 }
 
 lbm_status diagnostics(Ctx3* c, lbm_diag* d) {
     cudaError_t e;
     if (c->sb == 8)
-        e = launch_mass<double>((const double*)c->f[c->cur], c->info, (const double*)c->umac, c->nx, c->ny, c->nz,
-                                c->pitch, c->plane, c->mass_partial, c->mass_blocks, c->stream);
+        e = launch_mass<double>((const double*)c->f[c->cur], c->info, (const double*)c->umac, nullptr, c->nx, c->ny,
+                                c->nz, c->pitch, c->plane, c->mass_partial, c->mass_blocks, c->stream);
+    else if (c->sb == 2)
+        e = launch_mass<__half>((const __half*)c->f[c->cur], c->info, (const float*)c->umac, c->rref[c->cur], c->nx,
+                                c->ny, c->nz, c->pitch, c->plane, c->mass_partial, c->mass_blocks, c->stream);
     else
-        e = launch_mass<float>((const float*)c->f[c->cur], c->info, (const float*)c->umac, c->nx, c->ny, c->nz,
-                               c->pitch, c->plane, c->mass_partial, c->mass_blocks, c->stream);
+        e = launch_mass<float>((const float*)c->f[c->cur], c->info, (const float*)c->umac, nullptr, c->nx, c->ny,
+                               c->nz, c->pitch, c->plane, c->mass_partial, c->mass_blocks, c->stream);
     if (e != cudaSuccess) return fail3(c, nullptr, LBM_ERR_CUDA, std::string("diagnostics: ") + cudaGetErrorString(e));
     ++c->launches;
     std::vector<double> part((size_t)c->mass_blocks * 3);
