@@ -404,7 +404,7 @@ __device__ void face_reconstruct(const D3Args<S>& a, int fid, int x, int y, int 
 }
 
 template <typename S>
-__global__ void __launch_bounds__(256) d3q_pull_kernel(D3Args<S> a) {
+__global__ void __launch_bounds__(256, 4) d3q_pull_kernel(D3Args<S> a) {
     using R = typename Store<S>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -418,11 +418,38 @@ __global__ void __launch_bounds__(256) d3q_pull_kernel(D3Args<S> a) {
         return;
     }
     if ((info >> INFO3_FACE_SHIFT) & 7u) return;  // open-face nodes: d3q_face_pull_kernel
+    if constexpr (is_half<S>()) {
+        // sum w_i = 1: rho_k = rho_ref + the sum of the stored deviations
+        const long long sy = a.pitch, sz = (long long)a.ny * a.pitch;
+        const bool wrapped = (info & INFO3_WRAP) != 0;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        R f[Q];
-        pull<S, R>(a, k, x, y, z, info, f);
-        a.rho[(size_t)k * a.plane + n] = sum19(f);
+        for (int k = 0; k < 2; ++k) {
+            const S* __restrict__ fin = a.fin + (size_t)k * Q * a.plane;
+            float acc = 0.0f;
+            static_for<0, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                long long src;
+                int ii = i;
+                if (info & (1u << i)) {
+                    src = n;
+                    ii = opp_(i);
+                } else if (!wrapped) {
+                    src = n - ex_(i) - (long long)ey_(i) * sy - (long long)ez_(i) * sz;
+                } else {
+                    src = node_index(a, ex_(i) ? wrap(x - ex_(i), a.nx) : x, ey_(i) ? wrap(y - ey_(i), a.ny) : y,
+                                     ez_(i) ? wrap(z - ez_(i), a.nz) : z);
+                }
+                acc += __half2float(fin[(size_t)ii * a.plane + src]);
+            });
+            a.rho[(size_t)k * a.plane + n] = __half2float(a.rref_in[(size_t)k * a.plane + n]) + acc;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            R f[Q];
+            pull<S, R>(a, k, x, y, z, info, f);
+            a.rho[(size_t)k * a.plane + n] = sum19(f);
+        }
     }
 }
 
@@ -582,7 +609,7 @@ __device__ __forceinline__ void check_store_u(const D3Args<S>& a, long long n, t
 // normal velocity waits for the inward neighbour's, Eq. 22), and the inward
 // neighbours of the outlet hand theirs over with the flux terms of Eqs. 21, 23.
 template <typename S>
-__global__ void __launch_bounds__(256) d3q_collide_kernel(D3Args<S> a) {
+__global__ void __launch_bounds__(256, 3) d3q_collide_kernel(D3Args<S> a) {
     using R = typename Store<S>::R;
     __shared__ typename Pair<R>::type s_rr[HN];  // (rho_1, rho_2) of the tile and its halo, psi = 0 at solids
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
