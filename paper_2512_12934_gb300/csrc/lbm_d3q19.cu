@@ -574,15 +574,15 @@ __device__ __forceinline__ void add_j(const R (&f)[Q], R (&j)[3]) {
 // storage writes half(f*_i - w_i rho_ref), rho_ref being the half-rounded
 // density of component k at the node that pulls f*_i next step: x + e_i, or
 // x itself when that neighbour is solid or outside (halfway bounce-back).
-// dest_rho(I, k) returns that density.
+// dest_ref(I, k) returns that reference (already half-rounded).
 template <typename S, typename DestRho>
 __device__ __forceinline__ void store_pop(const D3Args<S>& a, int k, long long n, const typename Store<S>::R (&f)[Q],
-                                          DestRho dest_rho) {
+                                          DestRho dest_ref) {
     using R = typename Store<S>::R;
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         if constexpr (is_half<S>()) {
-            const R ref = half_round(dest_rho(I, k));
+            const R ref = dest_ref(I, k);
             a.fout[(size_t)(k * Q + i) * a.plane + n] = __float2half_rn(f[i] - ((R)w36_(i) / (R)36) * ref);
         } else {
             a.fout[(size_t)(k * Q + i) * a.plane + n] = (S)f[i];
@@ -609,9 +609,10 @@ __device__ __forceinline__ void check_store_u(const D3Args<S>& a, long long n, t
 // normal velocity waits for the inward neighbour's, Eq. 22), and the inward
 // neighbours of the outlet hand theirs over with the flux terms of Eqs. 21, 23.
 template <typename S>
-__global__ void __launch_bounds__(256, 3) d3q_collide_kernel(D3Args<S> a) {
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3) d3q_collide_kernel(D3Args<S> a) {
     using R = typename Store<S>::R;
     __shared__ typename Pair<R>::type s_rr[HN];  // (rho_1, rho_2) of the tile and its halo, psi = 0 at solids
+    __shared__ __half2 s_ref[is_half<S>() ? HN : 1];  // FP16 storage: the same densities rounded to half
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
     for (int q = tid; q < HN; q += TX * TY * TZ) {
@@ -622,6 +623,7 @@ __global__ void __launch_bounds__(256, 3) d3q_collide_kernel(D3Args<S> a) {
         v.y = m < 0 ? (R)0 : a.rho[a.plane + m];
         if (v.x < (R)(0.5 * SOLID_MARK)) v.x = (R)0;
         s_rr[q] = v;
+        if constexpr (is_half<S>()) s_ref[q] = __floats2half2_rn((float)v.x, (float)v.y);
     }
     __syncthreads();
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
@@ -706,8 +708,8 @@ __global__ void __launch_bounds__(256, 3) d3q_collide_kernel(D3Args<S> a) {
     auto dest_rho = [&](auto I, int k) -> R {
         constexpr int i = decltype(I)::value;
         const int h = (info & (1u << opp_(i))) ? hc : hc + ex_(i) + HX * (ey_(i) + HY * ez_(i));
-        const typename Pair<R>::type v = s_rr[h];
-        return k ? v.y : v.x;
+        const __half2 r = s_ref[h];
+        return k ? __high2float(r) : __low2float(r);
     };
     if constexpr (is_half<S>()) {
         a.rref_out[n] = __float2half_rn(r1);
@@ -763,7 +765,7 @@ __global__ void __launch_bounds__(128) d3q_outlet_kernel(D3Args<S> a) {
         constexpr int i = decltype(I)::value;
         long long m = n;
         if (!(info & (1u << opp_(i)))) m = site_index(a, c[0] + ex_(i), c[1] + ey_(i), c[2] + ez_(i));
-        return a.rho[(size_t)k * a.plane + m];
+        return half_round(a.rho[(size_t)k * a.plane + m]);
     };
     if constexpr (is_half<S>()) {
         a.rref_out[n] = __float2half_rn(r1);
