@@ -510,26 +510,30 @@ template <typename R, typename Site>
 __device__ __forceinline__ void stencil_sums(Site site, R (&g1)[3], R (&g2)[3]) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) g1[q] = g2[q] = (R)0;
-    static_for<0, 125>([&](auto C) {
+    // pairs (e, -e): g += w e (psi(x+e) - psi(x-e)); c runs over the half of
+    // the 5x5x5 cube before its centre (index 62), -e is site 124 - c
+    static_for<0, 62>([&](auto C) {
         constexpr int c = decltype(C)::value;
         constexpr int dx = c % 5 - 2, dy = (c / 5) % 5 - 2, dz = c / 25 - 2;
         constexpr int r2 = dx * dx + dy * dy + dz * dz;
         constexpr int wq = sw5040_(r2);
-        if constexpr (r2 != 0 && wq != 0) {
+        if constexpr (wq != 0) {
             const R w = (R)wq / (R)5040;
-            R r1, rr2;
-            site(dx, dy, dz, r1, rr2);
+            R p1, p2, m1, m2;
+            site(dx, dy, dz, p1, p2);
+            site(-dx, -dy, -dz, m1, m2);
+            const R d1 = p1 - m1, d2 = p2 - m2;
             if constexpr (dx != 0) {
-                g1[0] += (w * (R)dx) * r1;
-                g2[0] += (w * (R)dx) * rr2;
+                g1[0] += (w * (R)dx) * d1;
+                g2[0] += (w * (R)dx) * d2;
             }
             if constexpr (dy != 0) {
-                g1[1] += (w * (R)dy) * r1;
-                g2[1] += (w * (R)dy) * rr2;
+                g1[1] += (w * (R)dy) * d1;
+                g2[1] += (w * (R)dy) * d2;
             }
             if constexpr (dz != 0) {
-                g1[2] += (w * (R)dz) * r1;
-                g2[2] += (w * (R)dz) * rr2;
+                g1[2] += (w * (R)dz) * d1;
+                g2[2] += (w * (R)dz) * d2;
             }
         }
     });
@@ -615,9 +619,13 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : 3) d3q_collide_kerne
     __shared__ __half2 s_ref[is_half<S>() ? HN : 1];  // FP16 storage: the same densities rounded to half
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+    // tiles whose halo lies inside the grid need no wrap / mirror / wall resolution
+    const bool inner = x0 >= 2 && y0 >= 2 && z0 >= 2 && x0 + TX + 2 <= a.nx && y0 + TY + 2 <= a.ny &&
+                       z0 + TZ + 2 <= a.nz;
     for (int q = tid; q < HN; q += TX * TY * TZ) {
         const int hx = q % HX, hy = (q / HX) % HY, hz = q / (HX * HY);
-        const long long m = site_index(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz);
+        const long long m = inner ? node_index(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz)
+                                  : site_index(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz);
         typename Pair<R>::type v;
         v.x = m < 0 ? (R)SOLID_MARK : a.rho[m];
         v.y = m < 0 ? (R)0 : a.rho[a.plane + m];
