@@ -300,6 +300,95 @@ __global__ void __launch_bounds__(256) mlp_adam_kernel(float* __restrict__ param
     params[n] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
 }
 
+// ---- inference kernel: 128 samples per CTA, 8x8 register tiles -----------
+// Activations live feature-major in shared memory (act[k][s]); the hidden
+// weights are staged from a k-major copy (Wt[k][j]) with 16-byte loads, so a
+// thread's inner step reads two float4 of weights and two float4 of inputs
+// for 64 FMAs.
+constexpr int TB = 128;   // samples per CTA
+constexpr int NTB = 256;  // threads: 16 neuron groups x 16 sample groups of 8
+constexpr size_t SMEM_BIG = (size_t)(H * H + 2 * H * TB) * sizeof(float);
+
+// Wt[e][l][k][j] = W_{l+2}[j][k] for the two hidden 128x128 layers.
+__global__ void mlp_transpose_kernel(const float* __restrict__ params, float* __restrict__ wt) {
+    const int e = blockIdx.y;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;  // over 2 * H * H
+    if (q >= 2 * H * H) return;
+    const int l = q / (H * H), r = q % (H * H), k = r / H, j = r % H;
+    wt[(size_t)e * 2 * H * H + q] = params[(size_t)e * PS + (l ? oW3 : oW2) + j * H + k];
+}
+
+__global__ void __launch_bounds__(NTB) mlp_infer_kernel(const float* __restrict__ params,
+                                                         const float* __restrict__ wt, const float* __restrict__ X,
+                                                         int B, float* __restrict__ Y) {
+    extern __shared__ __align__(16) float smem[];
+    float* Wt = smem;              // [H][H]
+    float* actA = smem + H * H;    // [H][TB]
+    float* actB = actA + H * TB;   // [H][TB]
+    const int e = blockIdx.y, s0 = blockIdx.x * TB;
+    const float* p = params + (size_t)e * PS;
+    // layer 1 (K = 4): consecutive threads take consecutive samples
+    for (int q = threadIdx.x; q < TB * H; q += NTB) {
+        const int j = q / TB, sl = q % TB, b = s0 + sl;
+        float z = __ldg(p + ob1 + j);
+        if (b < B) {
+#pragma unroll
+            for (int k = 0; k < I; ++k) z = fmaf(__ldg(p + oW1 + j * I + k), __ldg(X + (size_t)b * I + k), z);
+        }
+        actA[j * TB + sl] = gelu(z);
+    }
+    const int ng = threadIdx.x % 16, sg = threadIdx.x / 16;
+    float* in = actA;
+    float* out = actB;
+#pragma unroll 1
+    for (int l = 0; l < 2; ++l) {
+        __syncthreads();  // the previous layer's outputs and reads of Wt are complete
+        const float4* src = reinterpret_cast<const float4*>(wt + ((size_t)e * 2 + l) * H * H);
+        for (int q = threadIdx.x; q < H * H / 4; q += NTB) reinterpret_cast<float4*>(Wt)[q] = __ldg(src + q);
+        __syncthreads();
+        const float* bias = p + (l ? ob3 : ob2);
+        float acc[8][8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float bc = __ldg(bias + 8 * ng + c);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) acc[r][c] = bc;
+        }
+#pragma unroll 2
+        for (int k = 0; k < H; ++k) {
+            const float4 w0 = reinterpret_cast<const float4*>(Wt + k * H + 8 * ng)[0];
+            const float4 w1 = reinterpret_cast<const float4*>(Wt + k * H + 8 * ng)[1];
+            const float4 a0 = reinterpret_cast<const float4*>(in + k * TB + 8 * sg)[0];
+            const float4 a1 = reinterpret_cast<const float4*>(in + k * TB + 8 * sg)[1];
+            const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], w[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float4* o = reinterpret_cast<float4*>(out + (8 * ng + c) * TB + 8 * sg);
+            o[0] = make_float4(gelu(acc[0][c]), gelu(acc[1][c]), gelu(acc[2][c]), gelu(acc[3][c]));
+            o[1] = make_float4(gelu(acc[4][c]), gelu(acc[5][c]), gelu(acc[6][c]), gelu(acc[7][c]));
+        }
+        float* t = in;
+        in = out;
+        out = t;
+    }
+    __syncthreads();
+    // layer 4: one thread per (sample, output)
+    {
+        const int sl = threadIdx.x % TB, o = threadIdx.x / TB, b = s0 + sl;
+        const float* w4 = p + oW4 + o * H;
+        float y = __ldg(p + ob4 + o);
+#pragma unroll 8
+        for (int k = 0; k < H; ++k) y = fmaf(in[k * TB + sl], __ldg(w4 + k), y);
+        if (b < B) Y[((size_t)e * B + b) * O + o] = y;
+    }
+}
+
 // Ensemble mean and relative spread (max over outputs of the population std
 // over members / |mean|), two passes over the members.
 __global__ void mlp_reduce_kernel(const float* __restrict__ Y, int E, int B, float* __restrict__ mean,
@@ -342,6 +431,7 @@ struct lbm_mlp {
     float* v = nullptr;
     int64_t t = 0;            // Adam steps taken
     uint64_t seed = 0;
+    float* wt = nullptr;      // [E][2][H][H] k-major copy of the hidden weights (inference)
     void* ws = nullptr;       // grow-only device workspace of the per-call buffers
     size_t ws_bytes = 0;
     std::string err;
@@ -371,6 +461,9 @@ cudaError_t set_smem_attrs() {
         if (g_attr_err == cudaSuccess)
             g_attr_err = cudaFuncSetAttribute(mlp_forward_kernel<false>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (g_attr_err == cudaSuccess)
+            g_attr_err = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)SMEM_BIG);
         if (g_attr_err == cudaSuccess)
             g_attr_err = cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)SMEM_BYTES);
@@ -441,6 +534,19 @@ lbm_status run_step(lbm_mlp* mm, Scratch& s, int B, const int* idx, bool adam, d
     return LBM_OK;
 }
 
+// Refresh the k-major copy of the hidden weights after any parameter change.
+lbm_status refresh_wt(lbm_mlp* mm) {
+    mlp_transpose_kernel<<<dim3((2 * H * H + 255) / 256, mm->E), 256, 0, mm->stream>>>(mm->params, mm->wt);
+    MCK(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status launch_infer(lbm_mlp* mm, const float* dX, int n, float* dY) {
+    mlp_infer_kernel<<<dim3((n + TB - 1) / TB, mm->E), NTB, SMEM_BIG, mm->stream>>>(mm->params, mm->wt, dX, n, dY);
+    MCK(cudaGetLastError());
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -463,6 +569,7 @@ lbm_status lbm_mlp_create(int members, uint64_t seed, void* cuda_stream, lbm_mlp
     if (e == cudaSuccess) e = cudaMalloc((void**)&mm->v, bytes);
     if (e == cudaSuccess) e = cudaMemset(mm->m, 0, bytes);
     if (e == cudaSuccess) e = cudaMemset(mm->v, 0, bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&mm->wt, (size_t)members * 2 * H * H * sizeof(float));
     if (e != cudaSuccess) {
         const std::string msg = std::string("mlp allocation: ") + cudaGetErrorString(e);
         lbm_mlp_destroy(mm);
@@ -490,6 +597,11 @@ lbm_status lbm_mlp_create(int members, uint64_t seed, void* cuda_stream, lbm_mlp
         lbm_mlp_destroy(mm);
         return mfail(nullptr, LBM_ERR_CUDA, msg);
     }
+    if (refresh_wt(mm) != LBM_OK) {
+        const std::string msg = mm->err;
+        lbm_mlp_destroy(mm);
+        return mfail(nullptr, LBM_ERR_CUDA, msg);
+    }
     *out = mm;
     return LBM_OK;
 }
@@ -502,7 +614,7 @@ lbm_status lbm_mlp_set_params(lbm_mlp* mm, const float* params) {
     MCK(cudaMemset(mm->m, 0, (size_t)mm->E * PS * sizeof(float)));
     MCK(cudaMemset(mm->v, 0, (size_t)mm->E * PS * sizeof(float)));
     mm->t = 0;
-    return LBM_OK;
+    return refresh_wt(mm);
 }
 
 lbm_status lbm_mlp_get_params(lbm_mlp* mm, float* params) {
@@ -518,9 +630,8 @@ lbm_status lbm_mlp_forward(lbm_mlp* mm, const float* X, int n, float* Y) {
     Scratch s;
     CARVE((size_t)n * I, 0, (size_t)mm->E * n * O, 0, 0, 0, 0);
     MCK(cudaMemcpyAsync(s.X, X, (size_t)n * I * sizeof(float), cudaMemcpyHostToDevice, mm->stream));
-    mlp_forward_kernel<false><<<dim3((n + TILE - 1) / TILE, mm->E), NTH, SMEM_BYTES, mm->stream>>>(
-        mm->params, s.X, nullptr, n, s.Y, nullptr);
-    MCK(cudaGetLastError());
+    lbm_status st = launch_infer(mm, s.X, n, s.Y);
+    if (st != LBM_OK) return st;
     MCK(cudaMemcpyAsync(Y, s.Y, (size_t)mm->E * n * O * sizeof(float), cudaMemcpyDeviceToHost, mm->stream));
     MCK(cudaStreamSynchronize(mm->stream));
     return LBM_OK;
@@ -567,6 +678,8 @@ lbm_status lbm_mlp_train(lbm_mlp* mm, const float* X, const float* T, int n, int
             if (st != LBM_OK) return st;
         }
     }
+    lbm_status st = refresh_wt(mm);
+    if (st != LBM_OK) return st;
     MCK(cudaStreamSynchronize(mm->stream));
     return LBM_OK;
 }
@@ -584,9 +697,8 @@ lbm_status lbm_mlp_predict(lbm_mlp* mm, const float* X, int n, float* mean, floa
         dm = s.T;
         ds = s.grad;
     }
-    mlp_forward_kernel<false><<<dim3((n + TILE - 1) / TILE, mm->E), NTH, SMEM_BYTES, mm->stream>>>(
-        mm->params, dX, nullptr, n, s.Y, nullptr);
-    MCK(cudaGetLastError());
+    lbm_status st = launch_infer(mm, dX, n, s.Y);
+    if (st != LBM_OK) return st;
     mlp_reduce_kernel<<<(n + 255) / 256, 256, 0, mm->stream>>>(s.Y, mm->E, n, dm, ds);
     MCK(cudaGetLastError());
     if (!dst_is_device) {
@@ -600,7 +712,7 @@ lbm_status lbm_mlp_predict(lbm_mlp* mm, const float* X, int n, float* mean, floa
 void lbm_mlp_destroy(lbm_mlp* mm) {
     if (!mm) return;
     if (mm->stream) cudaStreamSynchronize(mm->stream);
-    void* p[] = {mm->params, mm->m, mm->v, mm->ws};
+    void* p[] = {mm->params, mm->m, mm->v, mm->wt, mm->ws};
     for (void* q : p)
         if (q) cudaFree(q);
     delete mm;
