@@ -1129,7 +1129,7 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params, const lbm_
         *out = c;
         return LBM_OK;
     }
-    if (grid->lattice != LBM_D2Q9) return fail(nullptr, LBM_ERR_INVALID_ARG, "unknown lattice");
+    if (grid->lattice != LBM_D2Q9) return fail(nullptr, LBM_ERR_UNSUPPORTED, "unknown lattice");
     for (int f = 0; f < nbc; ++f)
         if (bcs && bcs[f].rho_profile)
             return fail(nullptr, LBM_ERR_UNSUPPORTED, "rho_profile is implemented for D3Q19 faces only");

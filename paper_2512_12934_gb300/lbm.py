@@ -215,14 +215,17 @@ class Solver:
             else:
                 BC[j].lo[0], BC[j].hi[0] = fc["lo"], fc["hi"]
                 npos = fc["hi"] - fc["lo"] + 1
+            # the library reads one inflow speed per face position of an inlet
+            # (outlets ignore it); extents it rejects are reported by the library
             prof = fc.get("profile")
-            prof = np.zeros(npos) if prof is None else prof
+            if fc["kind"] != "inlet" or prof is None:
+                prof = np.zeros(max(npos, 1))
             prof = np.ascontiguousarray(prof, dtype=np.float64).reshape(-1)
-            if prof.size != npos:
-                raise ValueError("face profile needs %d values" % npos)
+            if npos > 0 and prof.size != npos:
+                raise ValueError("inlet profile needs %d values, got %d" % (npos, prof.size))
             keep.append(prof)
             BC[j].u_profile = _dptr(prof)
-            if fc.get("rho_profile") is not None:
+            if fc["kind"] == "inlet" and fc.get("rho_profile") is not None:
                 rp = np.ascontiguousarray(fc["rho_profile"], dtype=np.float64).reshape(-1)
                 if rp.size != 2 * npos:
                     raise ValueError("face rho_profile needs %d values" % (2 * npos))
