@@ -214,10 +214,15 @@ cudaError_t launch_lists(lbm_ctx* c, bool macros, cudaStream_t st, cudaStream_t 
         e = cudaEventRecord(c->ev_fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(side, c->ev_fork, 0);
     }
+    // Forked (graph) steps launch the general list first: its CTAs are few
+    // but large (staging warps), and placed before the fast list fills the
+    // SMs they start at once instead of waiting for fast CTAs to drain.
+    D2Args<S, R> ag = a;
+    ag.list_off = c->nfast;
+    if (fork && e == cudaSuccess) e = launch_d2q9_step<S, R>(ag, c->variant, true, c->ngeneral, side);
     if (e == cudaSuccess) e = launch_d2q9_step<S, R>(a, c->variant, false, c->nfast, st);
     if (e == cudaSuccess && mid) e = cudaEventRecord(mid, st);
-    a.list_off = c->nfast;
-    if (e == cudaSuccess) e = launch_d2q9_step<S, R>(a, c->variant, true, c->ngeneral, fork ? side : st);
+    if (!fork && e == cudaSuccess) e = launch_d2q9_step<S, R>(ag, c->variant, true, c->ngeneral, st);
     if (fork && e == cudaSuccess) {
         e = cudaEventRecord(c->ev_join, side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join, 0);
@@ -946,9 +951,12 @@ cudaError_t batch_launch(lbm_batch* b, bool macros, cudaStream_t st, cudaStream_
         e = cudaEventRecord(b->ev_fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(side, b->ev_fork, 0);
     }
+    // general list first when forked (see launch_lists)
+    BatchArgs<S, R> ag = a;
+    ag.off = b->nfast;
+    if (fork && e == cudaSuccess) e = launch_d2q9_batch<S, R>(ag, b->variant, true, b->ngeneral, side);
     if (e == cudaSuccess) e = launch_d2q9_batch<S, R>(a, b->variant, false, b->nfast, st);
-    a.off = b->nfast;
-    if (e == cudaSuccess) e = launch_d2q9_batch<S, R>(a, b->variant, true, b->ngeneral, fork ? side : st);
+    if (!fork && e == cudaSuccess) e = launch_d2q9_batch<S, R>(ag, b->variant, true, b->ngeneral, st);
     if (fork && e == cudaSuccess) {
         e = cudaEventRecord(b->ev_join, side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->ev_join, 0);

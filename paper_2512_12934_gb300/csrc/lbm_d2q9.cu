@@ -173,15 +173,12 @@ __host__ __device__ constexpr bool unknown_(int side, int i) {
 
 // Open-face reconstruction of the unknown populations of a face node on side
 // SIDE: inlet Eq. 13/14 + alpha (Eqs. 15-19), outlet Eq. 20 with lambda.
+// g holds the pulled populations of the inward neighbour x - n.
 template <int SIDE, typename S, typename R>
-__device__ __forceinline__ void face_fix_side(const D2Args<S, R>& a, const FaceDev& F, int x, int y, R lam,
-                                              R (&f)[2][9]) {
+__device__ __forceinline__ void face_fix_with(const D2Args<S, R>& a, const FaceDev& F, int x, int y, R lam,
+                                              const R (&g)[2][9], R (&f)[2][9]) {
     constexpr int OX = side_ox(SIDE), OY = side_oy(SIDE);
     const int slot = F.base + ((SIDE <= 1) ? y : x) - F.lo;
-    const int x2 = x - OX, y2 = y - OY;  // inward neighbour
-    const unsigned info2 = a.info[y2 * a.pitch + x2];
-    R g[2][9];
-    pull_wrap(a, x2, y2, info2, g);
     if (F.kind == FACE_INLET) {
         const R* Fp = a.Fp_in + slot * 8;  // [node x1/x2][k][d]
         const R r20 = rho_of(g[0]), r21 = rho_of(g[1]);
@@ -220,6 +217,16 @@ __device__ __forceinline__ void face_fix_side(const D2Args<S, R>& a, const FaceD
 #pragma unroll
                 for (int k = 0; k < 2; ++k) f[k][i] = (fo[i * 2 + k] + lam * g[k][i]) * inv;
     }
+}
+
+template <int SIDE, typename S, typename R>
+__device__ __forceinline__ void face_fix_side(const D2Args<S, R>& a, const FaceDev& F, int x, int y, R lam,
+                                              R (&f)[2][9]) {
+    const int x2 = x - side_ox(SIDE), y2 = y - side_oy(SIDE);  // inward neighbour
+    const unsigned info2 = a.info[y2 * a.pitch + x2];
+    R g[2][9];
+    pull_wrap(a, x2, y2, info2, g);
+    face_fix_with<SIDE>(a, F, x, y, lam, g, f);
 }
 
 template <typename S, typename R>
@@ -446,61 +453,248 @@ __device__ __forceinline__ int strip_entry(int side, int gx, int gy, int x0, int
 // nodes of the tile's strips (inlet Eqs. 13-19 / outlet Eq. 20) once each;
 // own nodes and halo sites that are such face nodes read the result from
 // shared memory instead of repeating the reconstruction.
+// Barrier over the NT node threads of a tile.  General tiles launch extra
+// staging warps that leave after staging, so their later barriers name the
+// node threads only (barrier 1); fast tiles are exactly NT threads.
+template <bool GEN, int NT>
+__device__ __forceinline__ void tile_sync() {
+    if constexpr (GEN) asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    else __syncthreads();
+}
+
+// Thread roles of a general tile.  Threads [0, NT) own the tile's nodes;
+// [NT, NT + RING) each pull one halo-ring node; the warps from SB on
+// reconstruct the face strips (and fold lambda and chi, which only face
+// reconstruction needs).  The three groups pull concurrently, so a general
+// tile's staging latency is one chain of dependent loads instead of three.
+template <int TX, int TY>
+struct GenRoles {
+    static constexpr int NT = TX * TY;
+    static constexpr int RX = TX + 4, RY = TY + 4;
+    static constexpr int RING = RX * RY - NT;
+    static constexpr int SB = (NT + RING + 31) / 32 * 32;
+    static constexpr int SL = (TX > TY ? TX : TY) + 4;
+    static constexpr int THREADS = SB + (2 * SL + 31) / 32 * 32;
+    static_assert(THREADS <= 1024, "general tile exceeds a CTA");
+};
+
+// Halo-ring entry p as tile-local coordinates (two rows above, two below,
+// two columns on each side).
+template <int TX, int TY>
+__device__ __forceinline__ void ring_coords(int p, int& rx, int& ry) {
+    constexpr int RX = TX + 4;
+    if (p < 2 * RX) {
+        ry = p / RX;
+        rx = p % RX;
+    } else if (p < 4 * RX) {
+        ry = TY + 2 + (p - 2 * RX) / RX;
+        rx = (p - 2 * RX) % RX;
+    } else {
+        const int q = p - 4 * RX;
+        ry = 2 + q / 4;
+        const int c = q % 4;
+        rx = c < 2 ? c : TX + c;
+    }
+}
+
+// lambda (Eq. 21) and chi (Eq. 23) from the previous step's FP64 flux
+// partials, summed by one warp in a fixed order (per-lane strided sums, then
+// a shuffle tree to lane 0), so every warp of every tile gets the same bits.
+// The loads are issued first (begin) and summed later (finish), so that the
+// caller can put its own independent loads in between.
+struct LamFold {
+    double p[2][4];
+    double valid;
+};
+
+template <typename S, typename R>
+__device__ __forceinline__ void fold_begin(const D2Args<S, R>& a, LamFold& L) {
+    const int lane = threadIdx.x & 31;
+    L.valid = a.scal_in[5];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) L.p[h][j] = lane + 32 * h < a.nslots ? a.part_in[(lane + 32 * h) * 4 + j] : 0.0;
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void fold_finish(const D2Args<S, R>& a, const LamFold& L, double& lam, double& chi) {
+    const int lane = threadIdx.x & 31;
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (lane + 32 * h < a.nslots) t[j] += L.p[h][j];
+    for (int sl = lane + 64; sl < a.nslots; sl += 32)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[j] += a.part_in[sl * 4 + j];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t[j] += __shfl_down_sync(0xffffffffu, t[j], o);
+    lam = a.scal_in[0];
+    chi = a.scal_in[1];
+    if (L.valid != 0.0 && a.out_face >= 0 && t[3] > 0.0) {
+        const double um = t[2] / t[3];
+        lam = um > 0.0 ? um : 0.0;
+        chi = (!a.have_inlet || fabs(t[1]) < 1e-14) ? 1.0 : t[0] / t[1];
+    }
+    lam = __shfl_sync(0xffffffffu, lam, 0);
+    chi = __shfl_sync(0xffffffffu, chi, 0);
+}
+
 template <typename S, typename R, int TX, int TY>
 __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSmemGen<S, R, TX, TY>& sm, int x0,
-                                                   int y0, int tx, int ty, unsigned strips, unsigned bflags,
-                                                   R (&f)[2][9], unsigned& info, bool& fluid) {
-    constexpr int RX = TX + 4, RY = TY + 4, NT = TX * TY;
-    constexpr int RING = RX * RY - TX * TY;
+                                                   int y0, unsigned strips, unsigned bflags, R (&f)[2][9],
+                                                   unsigned& info, bool& fluid) {
+    using G = GenRoles<TX, TY>;
+    constexpr int NT = G::NT, RING = G::RING;
     const int tid = threadIdx.x;
-    // ---- lambda (Eq. 21) and chi (Eq. 23) from the previous step's FP64 flux
-    // partials: one warp, fixed order (the same in every tile that needs them)
-    if (bflags & BLOCK_LAMBDA) {
-        if (tid >= NT - 32) {
-            const int lane = tid & 31;
-            const bool valid = a.scal_in[5] != 0.0;
-            double t[4] = {0.0, 0.0, 0.0, 0.0};
-            if (valid)
-                for (int sl = lane; sl < a.nslots; sl += 32)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) t[j] += a.part_in[sl * 4 + j];
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) t[j] += __shfl_down_sync(0xffffffffu, t[j], o);
-            if (lane == 0) {
-                double lam = a.scal_in[0], chi = a.scal_in[1];
-                if (valid && a.out_face >= 0 && t[3] > 0.0) {
-                    const double um = t[2] / t[3];
-                    lam = um > 0.0 ? um : 0.0;
-                    chi = (!a.have_inlet || fabs(t[1]) < 1e-14) ? 1.0 : t[0] / t[1];
-                }
-                sm.lam = R(lam);
-                sm.chi = R(chi);
-            }
-        }
-        __syncthreads();
-    }
-    const R lam = (bflags & BLOCK_LAMBDA) ? sm.lam : R(0);
     const int side0 = (int)(strips & 0xffu) - 1, side1 = (int)((strips >> 8) & 0xffu) - 1;
-    const int len0 = side0 < 0 ? 0 : (side0 <= 1 ? RY : RX);
-    const int len1 = side1 < 0 ? 0 : (side1 <= 1 ? RY : RX);
+    const int len0 = side0 < 0 ? 0 : (side0 <= 1 ? G::RY : G::RX);
+    const int len1 = side1 < 0 ? 0 : (side1 <= 1 ? G::RY : G::RX);
     auto strip_of = [&](int side) { return side == side0 ? 0 : (side == side1 ? 1 : -1); };
 
-    // ---- phase 0: face strips ----
-    {
-        const int base = RING <= NT ? RING : 0;
-        for (int t = tid - base; t >= 0 && t < len0 + len1; t += NT) {
-            const int j = t < len0 ? 0 : 1;
-            const int e = j == 0 ? t : t - len0;
-            const int side = j == 0 ? side0 : side1;
-            int sx, sy;
+    info = INFO_SOLID;
+    fluid = false;
+    int own_strip = -1, own_idx = 0;
+    int def_j = -1, def_e = 0, def_rx = 0, def_ry = 0;
+    // a node whose pull needs lambda but lies outside the strips (a face node
+    // beyond two sides, a mirrored ghost site) waits for the second pass
+    bool pending = false;
+    int pend_x = 0, pend_y = 0, pend_rx = 0, pend_ry = 0;
+    unsigned pend_info = 0;
+
+    if (tid < NT) {
+        // ---- own node ----
+        const int tx = tid % TX, ty = tid / TX;
+        const int x = x0 + tx, y = y0 + ty;
+        R r0 = R(0), r1 = R(0);
+        unsigned char sol = 1;
+        if (x >= 0 && x < a.nx && y >= 0 && y < a.ny) {
+            info = a.info[y * a.pitch + x];
+            fluid = !(info & INFO_SOLID);
+            if (fluid) {
+                sol = 0;
+                const int fid = (int)((info >> INFO_FACE_SHIFT) & 7u);
+                if (fid) {
+                    const int side = a.face[fid - 1].side;
+                    own_strip = strip_of(side);
+                    own_idx = side <= 1 ? ty : tx;
+                    if (own_strip < 0) pending = true;
+                } else {
+                    pull_general(a, x, y, info, R(0), f);
+                    r0 = rho_of(f[0]);
+                    r1 = rho_of(f[1]);
+                }
+            }
+        } else {
+            pending = true;
+        }
+        pend_x = x;
+        pend_y = y;
+        pend_rx = tx + 2;
+        pend_ry = ty + 2;
+        sm.rho[0][ty + 2][tx + 2] = r0;
+        sm.rho[1][ty + 2][tx + 2] = r1;
+        sm.sol[ty + 2][tx + 2] = sol;
+    } else if (tid < NT + RING) {
+        // ---- halo ring: densities only ----
+        int rx, ry;
+        ring_coords<TX, TY>(tid - NT, rx, ry);
+        int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+        R h0 = R(0), h1 = R(0);
+        unsigned char hs = 1;
+        if (!resolve_site(a, gx, gy)) {
+            const unsigned inf = a.info[gy * a.pitch + gx];
+            if (!(inf & INFO_SOLID)) {
+                hs = 0;
+                const int fid = (int)((inf >> INFO_FACE_SHIFT) & 7u);
+                if (fid) {
+                    const int side = a.face[fid - 1].side;
+                    const int j = strip_of(side);
+                    const int e = j >= 0 ? strip_entry<TX, TY>(side, gx, gy, x0, y0, a.nx, a.ny) : -1;
+                    if (j >= 0 && e >= 0) {
+                        def_j = j;  // filled from the strip after the barrier
+                        def_e = e;
+                        def_rx = rx;
+                        def_ry = ry;
+                    } else {
+                        pending = true;
+                        pend_x = gx;
+                        pend_y = gy;
+                        pend_rx = rx;
+                        pend_ry = ry;
+                        pend_info = inf;
+                    }
+                } else {
+                    R g[2][9];
+                    pull_general(a, gx, gy, inf, R(0), g);
+                    h0 = rho_of(g[0]);
+                    h1 = rho_of(g[1]);
+                }
+            }
+        }
+        sm.rho[0][ry][rx] = h0;
+        sm.rho[1][ry][rx] = h1;
+        sm.sol[ry][rx] = hs;
+    } else if (tid >= G::SB) {
+        // ---- face strips (and lambda, chi) ----
+        // warp-uniform: the fold is a warp collective
+        const int t = tid - G::SB;
+        const bool lam_on = (bflags & BLOCK_LAMBDA) && (t < 32 || (t & ~31) < len0 + len1);
+        LamFold L;
+        if (lam_on) fold_begin(a, L);
+        const bool has = t < len0 + len1;
+        const int j = t < len0 ? 0 : 1;
+        const int e = j == 0 ? t : t - len0;
+        const int side = j == 0 ? side0 : side1;
+        int sx = -1, sy = -1;
+        unsigned inf = INFO_SOLID, inf2 = INFO_SOLID;
+        if (has) {
             strip_node<TX, TY>(side, e, x0, y0, a.nx, a.ny, sx, sy);
-            if (sx < 0 || sx >= a.nx || sy < 0 || sy >= a.ny) continue;
-            const unsigned inf = a.info[sy * a.pitch + sx];
-            if ((inf & INFO_SOLID) || !((inf >> INFO_FACE_SHIFT) & 7u)) continue;
-            R g[2][9];
-            pull_general(a, sx, sy, inf, lam, g);
+            if (sx >= 0 && sx < a.nx && sy >= 0 && sy < a.ny) {
+                inf = a.info[sy * a.pitch + sx];
+                // the inward neighbour along this strip's normal, read with
+                // the node's own word (a corner node may belong to the face of
+                // the other side; it is re-read below then)
+                const int x2 = sx - side_ox(side), y2 = sy - side_oy(side);
+                if (x2 >= 0 && x2 < a.nx && y2 >= 0 && y2 < a.ny) inf2 = a.info[y2 * a.pitch + x2];
+            }
+        }
+        // both pulls in flight before lambda is folded; only the blend of
+        // Eqs. 13-20 waits for it
+        const bool face = !(inf & INFO_SOLID) && ((inf >> INFO_FACE_SHIFT) & 7u);
+        const int fid = (int)((inf >> INFO_FACE_SHIFT) & 7u) - 1;
+        const int fside = face ? a.face[fid].side : 0;
+        R g[2][9], gn[2][9];
+        if (face) {
+            const int x2 = sx - side_ox(fside), y2 = sy - side_oy(fside);
+            if (fside != side) inf2 = a.info[y2 * a.pitch + x2];
+            pull_wrap(a, sx, sy, inf, g);
+            pull_wrap(a, x2, y2, inf2, gn);
+        }
+        R lam = R(0);
+        if (lam_on) {
+            double dl, dc;
+            fold_finish(a, L, dl, dc);
+            lam = R(dl);
+            if (t == 0) {
+                sm.lam = R(dl);
+                sm.chi = R(dc);
+            }
+        }
+        if (face) {
+            const FaceDev& F = a.face[fid];
+            switch (fside) {
+            case 0: face_fix_with<0>(a, F, sx, sy, lam, gn, g); break;
+            case 1: face_fix_with<1>(a, F, sx, sy, lam, gn, g); break;
+            case 2: face_fix_with<2>(a, F, sx, sy, lam, gn, g); break;
+            default: face_fix_with<3>(a, F, sx, sy, lam, gn, g); break;
+            }
+        }
+        if (has && face) {
             sm.fs_rho[j][e][0] = rho_of(g[0]);
             sm.fs_rho[j][e][1] = rho_of(g[1]);
             const int o = side <= 1 ? sy - y0 : sx - x0;
@@ -512,88 +706,36 @@ __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSm
                     for (int i = 0; i < 9; ++i) sm.fs_f[j][o][k * 9 + i] = g[k][i];
         }
     }
-
-    // ---- own node ----
-    const int x = x0 + tx, y = y0 + ty;
-    const bool inb = (x >= 0 && x < a.nx && y >= 0 && y < a.ny);
-    info = INFO_SOLID;
-    fluid = false;
-    int own_strip = -1, own_idx = 0;
-    R r0 = R(0), r1 = R(0);
-    unsigned char sol = 1;
-    if (inb) {
-        info = a.info[y * a.pitch + x];
-        fluid = !(info & INFO_SOLID);
-        if (fluid) {
-            const int fid = (int)((info >> INFO_FACE_SHIFT) & 7u);
-            if (fid) {
-                const int side = a.face[fid - 1].side;
-                own_strip = strip_of(side);
-                own_idx = side <= 1 ? ty : tx;
-            }
-            if (own_strip < 0) {
-                pull_general(a, x, y, info, lam, f);
-                r0 = rho_of(f[0]);
-                r1 = rho_of(f[1]);
-            }
-            sol = 0;
-        }
-    } else if (site_rho<S, R, 2>(a, x, y, r0, r1, lam)) {
-        sol = 0;
-    }
-    sm.rho[0][ty + 2][tx + 2] = r0;
-    sm.rho[1][ty + 2][tx + 2] = r1;
-    sm.sol[ty + 2][tx + 2] = sol;
-
-    // ---- halo ring ----
-    int def_j = -1, def_e = 0, def_rx = 0, def_ry = 0;
-    for (int p = tid; p < RING; p += NT) {
-        int rx, ry;
-        if (p < 2 * RX) {
-            ry = p / RX;
-            rx = p % RX;
-        } else if (p < 4 * RX) {
-            ry = TY + 2 + (p - 2 * RX) / RX;
-            rx = (p - 2 * RX) % RX;
-        } else {
-            const int q = p - 4 * RX;
-            ry = 2 + q / 4;
-            const int c = q % 4;
-            rx = c < 2 ? c : TX + c;
-        }
-        int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
-        R h0 = R(0), h1 = R(0);
-        unsigned char hs = 1;
-        if (!resolve_site(a, gx, gy)) {
-            const unsigned inf = a.info[gy * a.pitch + gx];
-            if (!(inf & INFO_SOLID)) {
-                hs = 0;
-                const int fid = (int)((inf >> INFO_FACE_SHIFT) & 7u);
-                int j = -1, e = -1;
-                if (fid) {
-                    const int side = a.face[fid - 1].side;
-                    j = strip_of(side);
-                    if (j >= 0) e = strip_entry<TX, TY>(side, gx, gy, x0, y0, a.nx, a.ny);
+    // ---- second pass: pulls that need lambda outside the strips ----
+    if (__syncthreads_or(pending)) {
+        if (pending) {
+            const R lam = (bflags & BLOCK_LAMBDA) ? sm.lam : R(0);
+            R r0 = R(0), r1 = R(0);
+            unsigned char sol = 1;
+            if (tid < NT) {
+                if (fluid) {
+                    pull_general(a, pend_x, pend_y, info, lam, f);
+                    r0 = rho_of(f[0]);
+                    r1 = rho_of(f[1]);
+                    sol = 0;
+                } else if (site_rho<S, R, 2>(a, pend_x, pend_y, r0, r1, lam)) {
+                    sol = 0;
                 }
-                if (j >= 0 && e >= 0 && RING <= NT) {
-                    def_j = j;  // filled from the strip after the barrier
-                    def_e = e;
-                    def_rx = rx;
-                    def_ry = ry;
-                } else {
-                    R g[2][9];
-                    pull_general(a, gx, gy, inf, lam, g);
-                    h0 = rho_of(g[0]);
-                    h1 = rho_of(g[1]);
-                }
+            } else {
+                R g[2][9];
+                pull_general(a, pend_x, pend_y, pend_info, lam, g);
+                r0 = rho_of(g[0]);
+                r1 = rho_of(g[1]);
+                sol = 0;
             }
+            sm.rho[0][pend_ry][pend_rx] = r0;
+            sm.rho[1][pend_ry][pend_rx] = r1;
+            sm.sol[pend_ry][pend_rx] = sol;
         }
-        sm.rho[0][ry][rx] = h0;
-        sm.rho[1][ry][rx] = h1;
-        sm.sol[ry][rx] = hs;
+        __syncthreads();
     }
-    __syncthreads();
     if (own_strip >= 0) {
+        const int tx = tid % TX, ty = tid / TX;
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
@@ -626,10 +768,12 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
     unsigned info;
     bool fluid;
     if constexpr (GEN)
-        stage_tile_general<S, R, TX, TY>(a, smx, x0, y0, tx, ty, strips, bflags, f, info, fluid);
+        stage_tile_general<S, R, TX, TY>(a, smx, x0, y0, strips, bflags, f, info, fluid);
     else if (bflags & BLOCK_EDGE) stage_tile<S, R, TX, TY, 1>(a, sm, x0, y0, tx, ty, f, info, fluid);
     else stage_tile<S, R, TX, TY, 0>(a, sm, x0, y0, tx, ty, f, info, fluid);
     __syncthreads();
+    // general tiles: the ring and strip warps are done once the tile is staged
+    if (GEN && tid >= NT) return;
 
     const R rho0 = sm.rho[0][ty + 2][tx + 2], rho1 = sm.rho[1][ty + 2][tx + 2];
     R Fx0 = R(0), Fy0 = R(0), Fx1 = R(0), Fy1 = R(0);
@@ -693,7 +837,7 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
         if (covers && OF.chi) {
             const int along = (OF.side <= 1) ? ty : tx;
             if (fluid && nbr_face == a.out_face) sm.un[along] = (OF.side <= 1) ? ux : uy;
-            __syncthreads();
+            tile_sync<GEN, NT>();
             if (fluid && own_face == a.out_face) {
                 const R chi = sm.chi;
                 if (OF.side <= 1) ux = chi * sm.un[along];
@@ -831,7 +975,7 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
                 for (int j = 0; j < 4; ++j) smx.fl[wq][rk][j] = v[j];
             }
             if (lane == 0) smx.fcnt[wq] = __popc(bal);
-            __syncthreads();
+            tile_sync<GEN, NT>();
             if (tid < 4) {
                 // plain stores: the next step's outlet tiles read them after the
                 // kernel boundary, so no fence or atomic is needed
@@ -847,7 +991,7 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
 
 // Single-instance step: one tile of the launch's list per CTA.
 template <typename S, typename R, int TX, int TY, bool GEN>
-__global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
+__global__ void __launch_bounds__(GEN ? GenRoles<TX, TY>::THREADS : TX * TY) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
     const int li = a.list_off + blockIdx.x;
     step_tile<S, R, TX, TY, GEN>(a, a.blocks[li], a.block_flags[li], GEN ? a.block_strips[li] : 0u,
                                  GEN ? a.block_slot[li] : -1);
@@ -857,7 +1001,7 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
 // copies its instance's arguments into shared memory and runs the same tile
 // code, so a batch step equals stepping every member on its own.
 template <typename S, typename R, int TX, int TY, bool GEN>
-__global__ void __launch_bounds__(TX * TY) d2q9_batch_kernel(const __grid_constant__ BatchArgs<S, R> b) {
+__global__ void __launch_bounds__(GEN ? GenRoles<TX, TY>::THREADS : TX * TY) d2q9_batch_kernel(const __grid_constant__ BatchArgs<S, R> b) {
     __shared__ D2Args<S, R> sa;
     const int li = b.off + blockIdx.x;
     const int m = b.member[li];
@@ -951,13 +1095,13 @@ int d2q9_num_variants() { return (int)(sizeof(kVariants) / sizeof(kVariants[0]))
 
 template <typename S, typename R, int TX, int TY>
 static void launch_tile(const D2Args<S, R>& a, bool general, int nblocks, cudaStream_t st) {
-    if (general) d2q9_step_kernel<S, R, TX, TY, true><<<nblocks, TX * TY, 0, st>>>(a);
+    if (general) d2q9_step_kernel<S, R, TX, TY, true><<<nblocks, GenRoles<TX, TY>::THREADS, 0, st>>>(a);
     else d2q9_step_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(a);
 }
 
 template <typename S, typename R, int TX, int TY>
 static void launch_batch_tile(const BatchArgs<S, R>& b, bool general, int nblocks, cudaStream_t st) {
-    if (general) d2q9_batch_kernel<S, R, TX, TY, true><<<nblocks, TX * TY, 0, st>>>(b);
+    if (general) d2q9_batch_kernel<S, R, TX, TY, true><<<nblocks, GenRoles<TX, TY>::THREADS, 0, st>>>(b);
     else d2q9_batch_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(b);
 }
 
