@@ -517,6 +517,9 @@ __device__ __forceinline__ void fold_begin(const D2Args<S, R>& a, LamFold& L) {
         for (int j = 0; j < 4; ++j) L.p[h][j] = lane + 32 * h < a.nslots ? a.part_in[(lane + 32 * h) * 4 + j] : 0.0;
 }
 
+// The two quotients are taken in the tile's arithmetic precision R (the
+// partial sums stay FP64): FP64 division is a long sequence on GB300's FP64
+// pipe, and lambda and chi enter the step as R anyway.
 template <typename S, typename R>
 __device__ __forceinline__ void fold_finish(const D2Args<S, R>& a, const LamFold& L, double& lam, double& chi) {
     const int lane = threadIdx.x & 31;
@@ -536,9 +539,9 @@ __device__ __forceinline__ void fold_finish(const D2Args<S, R>& a, const LamFold
     lam = a.scal_in[0];
     chi = a.scal_in[1];
     if (L.valid != 0.0 && a.out_face >= 0 && t[3] > 0.0) {
-        const double um = t[2] / t[3];
-        lam = um > 0.0 ? um : 0.0;
-        chi = (!a.have_inlet || fabs(t[1]) < 1e-14) ? 1.0 : t[0] / t[1];
+        const R um = R(t[2]) / R(t[3]);
+        lam = um > R(0) ? double(um) : 0.0;
+        chi = (!a.have_inlet || fabs(t[1]) < 1e-14) ? 1.0 : double(R(t[0]) / R(t[1]));
     }
     lam = __shfl_sync(0xffffffffu, lam, 0);
     chi = __shfl_sync(0xffffffffu, chi, 0);
@@ -643,9 +646,9 @@ __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSm
         // ---- face strips (and lambda, chi) ----
         // warp-uniform: the fold is a warp collective
         const int t = tid - G::SB;
-        const bool lam_on = (bflags & BLOCK_LAMBDA) && (t < 32 || (t & ~31) < len0 + len1);
+        const bool lam_on = (bflags & BLOCK_LAMBDA) != 0;
         LamFold L;
-        if (lam_on) fold_begin(a, L);
+        if (lam_on && t < 32) fold_begin(a, L);
         const bool has = t < len0 + len1;
         const int j = t < len0 ? 0 : 1;
         const int e = j == 0 ? t : t - len0;
@@ -677,13 +680,18 @@ __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSm
         }
         R lam = R(0);
         if (lam_on) {
-            double dl, dc;
-            fold_finish(a, L, dl, dc);
-            lam = R(dl);
-            if (t == 0) {
-                sm.lam = R(dl);
-                sm.chi = R(dc);
+            // the first strip warp folds; the others read its result (the
+            // block flags are tile-uniform, so every strip warp gets here)
+            if (t < 32) {
+                double dl, dc;
+                fold_finish(a, L, dl, dc);
+                if (t == 0) {
+                    sm.lam = R(dl);
+                    sm.chi = R(dc);
+                }
             }
+            asm volatile("bar.sync 2, %0;" ::"n"(G::THREADS - G::SB) : "memory");
+            lam = sm.lam;
         }
         if (face) {
             const FaceDev& F = a.face[fid];
@@ -989,19 +997,39 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
     }
 }
 
+// Register cap of a general tile, within the 64 K register file for every
+// variant.  FP32 keeps 80 (measured on GB300: a 64-register cap spilled
+// ~0.5 KB per thread and made the step 20 % slower, although it would leave
+// room for a fifth fast tile on the SM).
+template <typename R, int TX, int TY>
+__host__ __device__ constexpr int gen_maxreg() {
+    constexpr int fit = 65536 / GenRoles<TX, TY>::THREADS / 8 * 8;
+    constexpr int want = sizeof(R) == 4 ? 80 : 128;
+    return want < fit ? want : fit;
+}
+
 // Single-instance step: one tile of the launch's list per CTA.
 template <typename S, typename R, int TX, int TY, bool GEN>
-__global__ void __launch_bounds__(GEN ? GenRoles<TX, TY>::THREADS : TX * TY) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
+__global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
+    static_assert(!GEN, "general tiles run d2q9_general_kernel");
     const int li = a.list_off + blockIdx.x;
-    step_tile<S, R, TX, TY, GEN>(a, a.blocks[li], a.block_flags[li], GEN ? a.block_strips[li] : 0u,
-                                 GEN ? a.block_slot[li] : -1);
+    step_tile<S, R, TX, TY, false>(a, a.blocks[li], a.block_flags[li], 0u, -1);
+}
+
+template <typename S, typename R, int TX, int TY>
+__global__ void __maxnreg__((gen_maxreg<R, TX, TY>())) d2q9_general_kernel(const __grid_constant__ D2Args<S, R> a) {
+    const int li = a.list_off + blockIdx.x;
+    step_tile<S, R, TX, TY, true>(a, a.blocks[li], a.block_flags[li], a.block_strips[li], a.block_slot[li]);
 }
 
 // Batched step: the list interleaves the tiles of many instances; each CTA
 // copies its instance's arguments into shared memory and runs the same tile
 // code, so a batch step equals stepping every member on its own.
+// Batched step: the list interleaves the tiles of many instances; each CTA
+// copies its instance's arguments into shared memory and runs the same tile
+// code, so a batch step equals stepping every member on its own.
 template <typename S, typename R, int TX, int TY, bool GEN>
-__global__ void __launch_bounds__(GEN ? GenRoles<TX, TY>::THREADS : TX * TY) d2q9_batch_kernel(const __grid_constant__ BatchArgs<S, R> b) {
+__device__ __forceinline__ void batch_tile(const BatchArgs<S, R>& b) {
     __shared__ D2Args<S, R> sa;
     const int li = b.off + blockIdx.x;
     const int m = b.member[li];
@@ -1013,6 +1041,16 @@ __global__ void __launch_bounds__(GEN ? GenRoles<TX, TY>::THREADS : TX * TY) d2q
     }
     __syncthreads();
     step_tile<S, R, TX, TY, GEN>(sa, b.blocks[li], b.flags[li], b.strips[li], b.slot[li]);
+}
+
+template <typename S, typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) d2q9_batch_kernel(const __grid_constant__ BatchArgs<S, R> b) {
+    batch_tile<S, R, TX, TY, false>(b);
+}
+
+template <typename S, typename R, int TX, int TY>
+__global__ void __maxnreg__((gen_maxreg<R, TX, TY>())) d2q9_batch_general_kernel(const __grid_constant__ BatchArgs<S, R> b) {
+    batch_tile<S, R, TX, TY, true>(b);
 }
 
 // FP64 mass / speed reduction for diagnostics.
@@ -1095,14 +1133,14 @@ int d2q9_num_variants() { return (int)(sizeof(kVariants) / sizeof(kVariants[0]))
 
 template <typename S, typename R, int TX, int TY>
 static void launch_tile(const D2Args<S, R>& a, bool general, int nblocks, cudaStream_t st) {
-    if (general) d2q9_step_kernel<S, R, TX, TY, true><<<nblocks, GenRoles<TX, TY>::THREADS, 0, st>>>(a);
+    if (general) d2q9_general_kernel<S, R, TX, TY><<<nblocks, GenRoles<TX, TY>::THREADS, 0, st>>>(a);
     else d2q9_step_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(a);
 }
 
 template <typename S, typename R, int TX, int TY>
 static void launch_batch_tile(const BatchArgs<S, R>& b, bool general, int nblocks, cudaStream_t st) {
-    if (general) d2q9_batch_kernel<S, R, TX, TY, true><<<nblocks, GenRoles<TX, TY>::THREADS, 0, st>>>(b);
-    else d2q9_batch_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(b);
+    if (general) d2q9_batch_general_kernel<S, R, TX, TY><<<nblocks, GenRoles<TX, TY>::THREADS, 0, st>>>(b);
+    else d2q9_batch_kernel<S, R, TX, TY><<<nblocks, TX * TY, 0, st>>>(b);
 }
 
 template <typename S, typename R>
