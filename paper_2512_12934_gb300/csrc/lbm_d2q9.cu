@@ -498,53 +498,48 @@ __device__ __forceinline__ void ring_coords(int p, int& rx, int& ry) {
 }
 
 // lambda (Eq. 21) and chi (Eq. 23) from the previous step's FP64 flux
-// partials, summed by one warp in a fixed order (per-lane strided sums, then
-// a shuffle tree to lane 0), so every warp of every tile gets the same bits.
-// The loads are issued first (begin) and summed later (finish), so that the
-// caller can put its own independent loads in between.
+// partials (four terms per slot), summed by one warp in a fixed order so that
+// every tile gets the same bits: lane 8j + c sums term j over slots c, c + 8,
+// c + 16, ... in order, then the eight chains of a term are added in a
+// three-level tree.  GB300's FP64 pipe is narrow, so the FP64 instruction
+// count (11 adds per lane) sets this fold's latency.  The loads are issued
+// first (begin) and summed later (finish), so that the caller can put its
+// own independent loads in between.
 struct LamFold {
-    double p[2][4];
+    double p[8];
     double valid;
 };
 
 template <typename S, typename R>
 __device__ __forceinline__ void fold_begin(const D2Args<S, R>& a, LamFold& L) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, j = lane >> 3, c = lane & 7;
     L.valid = a.scal_in[5];
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) L.p[h][j] = lane + 32 * h < a.nslots ? a.part_in[(lane + 32 * h) * 4 + j] : 0.0;
+    for (int k = 0; k < 8; ++k) L.p[k] = c + 8 * k < a.nslots ? a.part_in[(c + 8 * k) * 4 + j] : 0.0;
 }
 
-// The two quotients are taken in the tile's arithmetic precision R (the
-// partial sums stay FP64): FP64 division is a long sequence on GB300's FP64
-// pipe, and lambda and chi enter the step as R anyway.
 template <typename S, typename R>
 __device__ __forceinline__ void fold_finish(const D2Args<S, R>& a, const LamFold& L, double& lam, double& chi) {
-    const int lane = threadIdx.x & 31;
-    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    const int lane = threadIdx.x & 31, j = lane >> 3, c = lane & 7;
+    double t = 0.0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int k = 0; k < 8; ++k)
+        if (c + 8 * k < a.nslots) t += L.p[k];
+    for (int sl = c + 64; sl < a.nslots; sl += 8) t += a.part_in[sl * 4 + j];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (lane + 32 * h < a.nslots) t[j] += L.p[h][j];
-    for (int sl = lane + 64; sl < a.nslots; sl += 32)
+    for (int o = 4; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    double T[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) t[j] += a.part_in[sl * 4 + j];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t[j] += __shfl_down_sync(0xffffffffu, t[j], o);
+    for (int q = 0; q < 4; ++q) T[q] = __shfl_sync(0xffffffffu, t, 8 * q);
+    // the quotients are taken in the tile's arithmetic precision R, which
+    // is where lambda and chi are used
     lam = a.scal_in[0];
     chi = a.scal_in[1];
-    if (L.valid != 0.0 && a.out_face >= 0 && t[3] > 0.0) {
-        const R um = R(t[2]) / R(t[3]);
+    if (L.valid != 0.0 && a.out_face >= 0 && T[3] > 0.0) {
+        const R um = R(T[2]) / R(T[3]);
         lam = um > R(0) ? double(um) : 0.0;
-        chi = (!a.have_inlet || fabs(t[1]) < 1e-14) ? 1.0 : double(R(t[0]) / R(t[1]));
+        chi = (!a.have_inlet || fabs(T[1]) < 1e-14) ? 1.0 : double(R(T[0]) / R(T[1]));
     }
-    lam = __shfl_sync(0xffffffffu, lam, 0);
-    chi = __shfl_sync(0xffffffffu, chi, 0);
 }
 
 template <typename S, typename R, int TX, int TY>
