@@ -647,6 +647,11 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 4 
     using R = typename Store<S>::R;
     __shared__ typename Pair<R>::type s_rr[HN];  // (rho_1, rho_2) of the tile and its halo, psi = 0 at solids
     __shared__ __half2 s_ref[is_half<S>() ? HN : 1];  // FP16 storage: the same densities rounded to half
+    // component 0's pulled populations, kept for its collision after
+    // component 1's (FP32 arithmetic; FP64 pulls them again, its tile would
+    // exceed the static shared-memory limit)
+    constexpr bool STASH = sizeof(R) == 4;
+    __shared__ R s_f0[STASH ? Q : 1][STASH ? TX * TY * TZ : 1];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
     // tiles whose halo lies inside the grid need no wrap / mirror / wall resolution
@@ -686,6 +691,11 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 4 
     const R rt = r1 + r2;
     if (fid == 0) {
         add_j(f, j);
+        if constexpr (STASH)
+            static_for<0, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                s_f0[i][tid] = f[i];
+            });
         pull<S, R>(a, 1, x, y, z, info, f);
         add_j(f, j);
     } else {
@@ -749,11 +759,17 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 4 
         a.rref_out[n] = __float2half_rn(r1);
         a.rref_out[a.plane + n] = __float2half_rn(r2);
     }
-    // collide component 1 (still in registers), then reload component 0
+    // collide component 1 (still in registers), then component 0 (from the
+    // shared-memory copy in FP32, pulled again in FP64)
     collide<R>(f, r2, u[0], u[1], u[2], F2[0], F2[1], F2[2], a.s[1]);
     store_pop<S>(a, 1, n, f, dest_rho);
     if (fid == 0) {
-        pull<S, R>(a, 0, x, y, z, info, f);
+        if constexpr (STASH)
+            static_for<0, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                f[i] = s_f0[i][tid];
+            });
+        else pull<S, R>(a, 0, x, y, z, info, f);
     } else {
         const R* ff = a.fface + (size_t)slot * 2 * Q;
         static_for<0, Q>([&](auto I) {
