@@ -752,6 +752,90 @@ __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSm
     }
 }
 
+// Eq. 1 for both components of one node in moment space (T of Eq. 3, S of
+// Eq. 4), delta form: post-collision moment increments -s (m - m_eq) +
+// (1 - s/2) F_m, back-transformed with T^-1 = T^T diag(1/9, 1/36, 1/36, 1/6,
+// 1/12, 1/6, 1/12, 1/4, 1/4), with both components of an FP32 node in the
+// two lanes of each packed FP32x2 instruction (each lane rounds as the
+// scalar operation does).
+template <typename V>
+struct Lanes;
+template <>
+struct Lanes<float2> {
+    static __device__ __forceinline__ float2 c(float v) { return make_float2(v, v); }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, c(-1.f), a); }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 d) { return __ffma2_rn(a, b, d); }
+};
+// g: populations, r: density, fx, fy: force, s[1..8]: rates; ux, uy common.
+template <typename V>
+__device__ __forceinline__ void collide_lanes(const V (&g)[9], V r, V fx, V fy, const V (&s)[9], V ux, V uy, V uu3,
+                                              V (&o)[9]) {
+    using L = Lanes<V>;
+    const V d13 = L::sub(g[1], g[3]), d24 = L::sub(g[2], g[4]), d57 = L::sub(g[5], g[7]), d86 = L::sub(g[8], g[6]);
+    const V a13 = L::add(g[1], g[3]), a24 = L::add(g[2], g[4]), a57 = L::add(g[5], g[7]), a68 = L::add(g[6], g[8]);
+    const V sa = L::add(a13, a24), sd = L::add(a57, a68);
+    const V me = L::fma(L::c(-4), g[0], L::sub(L::mul(L::c(2), sd), sa));
+    const V mp = L::fma(L::c(4), g[0], L::fma(L::c(-2), sa, sd));
+    const V dpn = L::add(d57, d86), dmn = L::sub(d57, d86);
+    const V mjx = L::add(d13, dpn), mqx = L::fma(L::c(-2), d13, dpn);
+    const V mjy = L::add(d24, dmn), mqy = L::fma(L::c(-2), d24, dmn);
+    const V mxx = L::sub(a13, a24), mxy = L::sub(a57, a68);
+    const V uF = L::fma(ux, fx, L::mul(uy, fy));
+    V h[9], ns[9];
+#pragma unroll
+    for (int j = 1; j < 9; ++j) {
+        h[j] = L::fma(L::c(-0.5), s[j], L::c(1));
+        ns[j] = L::mul(L::c(-1), s[j]);
+    }
+    const V de = L::fma(ns[1], L::sub(me, L::mul(r, L::sub(uu3, L::c(2)))), L::mul(h[1], L::mul(L::c(6), uF)));
+    const V dp = L::fma(ns[2], L::sub(mp, L::mul(r, L::sub(L::c(1), uu3))), L::mul(h[2], L::mul(L::c(-6), uF)));
+    const V djx = L::fma(ns[3], L::sub(mjx, L::mul(r, ux)), L::mul(h[3], fx));
+    const V dqx = L::fma(ns[4], L::add(mqx, L::mul(r, ux)), L::mul(L::mul(L::c(-1), h[4]), fx));
+    const V djy = L::fma(ns[5], L::sub(mjy, L::mul(r, uy)), L::mul(h[5], fy));
+    const V dqy = L::fma(ns[6], L::add(mqy, L::mul(r, uy)), L::mul(L::mul(L::c(-1), h[6]), fy));
+    const V dxx = L::fma(ns[7], L::sub(mxx, L::mul(r, L::sub(L::mul(ux, ux), L::mul(uy, uy)))),
+                         L::mul(h[7], L::mul(L::c(2), L::sub(L::mul(ux, fx), L::mul(uy, fy)))));
+    const V dxy = L::fma(ns[8], L::sub(mxy, L::mul(L::mul(r, ux), uy)), L::mul(h[8], L::fma(ux, fy, L::mul(uy, fx))));
+    const V ce = L::mul(de, L::c(1.0 / 36.0)), cp = L::mul(dp, L::c(1.0 / 36.0));
+    const V cjx = L::mul(djx, L::c(1.0 / 6.0)), cqx = L::mul(dqx, L::c(1.0 / 12.0));
+    const V cjy = L::mul(djy, L::c(1.0 / 6.0)), cqy = L::mul(dqy, L::c(1.0 / 12.0));
+    const V cxx = L::mul(dxx, L::c(0.25)), cxy = L::mul(dxy, L::c(0.25));
+    const V ax_ = L::fma(L::c(-2), cp, L::mul(L::c(-1), ce)), dg = L::fma(L::c(2), ce, cp);
+    const V bx = L::fma(L::c(-2), cqx, cjx), by = L::fma(L::c(-2), cqy, cjy);
+    const V px = L::add(cjx, cqx), py = L::add(cjy, cqy);
+    o[0] = L::fma(L::c(4), L::sub(cp, ce), g[0]);
+    o[1] = L::add(g[1], L::add(L::add(ax_, bx), cxx));
+    o[2] = L::add(g[2], L::sub(L::add(ax_, by), cxx));
+    o[3] = L::add(g[3], L::add(L::sub(ax_, bx), cxx));
+    o[4] = L::add(g[4], L::sub(L::sub(ax_, by), cxx));
+    o[5] = L::add(g[5], L::add(L::add(L::add(dg, px), py), cxy));
+    o[6] = L::add(g[6], L::sub(L::add(L::sub(dg, px), py), cxy));
+    o[7] = L::add(g[7], L::add(L::sub(L::sub(dg, px), py), cxy));
+    o[8] = L::add(g[8], L::sub(L::sub(L::add(dg, px), py), cxy));
+}
+
+template <typename A>
+__device__ __forceinline__ void collide_pair(const A& a, const float (&f)[2][9], float rho0, float rho1, float ux,
+                                             float uy, float Fx0, float Fy0, float Fx1, float Fy1,
+                                             float (&o)[2][9]) {
+    const float uu3 = 3.f * (ux * ux + uy * uy);
+    float2 g[9], s[9], out[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        g[i] = make_float2(f[0][i], f[1][i]);
+        s[i] = make_float2(a.s[0][i], a.s[1][i]);
+    }
+    collide_lanes<float2>(g, make_float2(rho0, rho1), make_float2(Fx0, Fx1), make_float2(Fy0, Fy1), s,
+                          make_float2(ux, ux), make_float2(uy, uy), make_float2(uu3, uu3), out);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        o[0][i] = out[i].x;
+        o[1][i] = out[i].y;
+    }
+}
+
 // One tile of one step.  bxy = bx | by << 16; bflags = BLOCK_* flags; strips
 // and slot are used by general tiles only.
 template <typename S, typename R, int TX, int TY, bool GEN>
@@ -880,63 +964,89 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
             a.macro[3 * a.plane + n] = uy;
         }
         // ---- Eq. 1 in moment space (T of Eq. 3, S of Eq. 4), delta form ----
-        const R uu3 = R(3) * (ux * ux + uy * uy);
+        // General tiles (latency-bound) run both components through packed
+        // FP32x2 operations; fast tiles (issue- and HBM-bound) measured faster
+        // with the scalar form.
+        if constexpr (GEN && std::is_same<R, float>::value) {
+            R o2[2][9];
+            collide_pair(a, f, rho0, rho1, ux, uy, Fx0, Fy0, Fx1, Fy1, o2);
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const R* s = a.s[k];
-            const R r = k == 0 ? rho0 : rho1;
-            const R fx = k == 0 ? Fx0 : Fx1, fy = k == 0 ? Fy0 : Fy1;
-            const R* g = f[k];
-            const R d13 = g[1] - g[3], d24 = g[2] - g[4], d57 = g[5] - g[7], d86 = g[8] - g[6];
-            const R a13 = g[1] + g[3], a24 = g[2] + g[4], a57 = g[5] + g[7], a68 = g[6] + g[8];
-            const R sa = a13 + a24, sd = a57 + a68;
-            const R me = (R(2) * sd - sa) - R(4) * g[0];
-            const R mp = (sd - R(2) * sa) + R(4) * g[0];
-            const R mjx = d13 + (d57 + d86), mqx = (d57 + d86) - R(2) * d13;
-            const R mjy = d24 + (d57 - d86), mqy = (d57 - d86) - R(2) * d24;
-            const R mxx = a13 - a24, mxy = a57 - a68;
-            const R uF = ux * fx + uy * fy;
-            // post-collision moment increments: -s (m - m_eq) + (1 - s/2) F_m
-            const R de = -s[1] * (me - r * (uu3 - R(2))) + (R(1) - R(0.5) * s[1]) * (R(6) * uF);
-            const R dp = -s[2] * (mp - r * (R(1) - uu3)) + (R(1) - R(0.5) * s[2]) * (R(-6) * uF);
-            const R djx = -s[3] * (mjx - r * ux) + (R(1) - R(0.5) * s[3]) * fx;
-            const R dqx = -s[4] * (mqx + r * ux) - (R(1) - R(0.5) * s[4]) * fx;
-            const R djy = -s[5] * (mjy - r * uy) + (R(1) - R(0.5) * s[5]) * fy;
-            const R dqy = -s[6] * (mqy + r * uy) - (R(1) - R(0.5) * s[6]) * fy;
-            const R dxx = -s[7] * (mxx - r * (ux * ux - uy * uy)) +
-                          (R(1) - R(0.5) * s[7]) * (R(2) * (ux * fx - uy * fy));
-            const R dxy = -s[8] * (mxy - r * ux * uy) + (R(1) - R(0.5) * s[8]) * (ux * fy + uy * fx);
-            // back-transform T^-1 = T^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-            const R ce = de * R(1.0 / 36.0), cp = dp * R(1.0 / 36.0);
-            const R cjx = djx * R(1.0 / 6.0), cqx = dqx * R(1.0 / 12.0);
-            const R cjy = djy * R(1.0 / 6.0), cqy = dqy * R(1.0 / 12.0);
-            const R cxx = dxx * R(0.25), cxy = dxy * R(0.25);
-            const R ax_ = -ce - R(2) * cp, dg = R(2) * ce + cp;
-            const R bx = cjx - R(2) * cqx, by = cjy - R(2) * cqy;
-            const R px = cjx + cqx, py = cjy + cqy;
-            R o[9];
-            o[0] = g[0] + (R(4) * (cp - ce));
-            o[1] = g[1] + (ax_ + bx + cxx);
-            o[2] = g[2] + (ax_ + by - cxx);
-            o[3] = g[3] + (ax_ - bx + cxx);
-            o[4] = g[4] + (ax_ - by - cxx);
-            o[5] = g[5] + (dg + px + py + cxy);
-            o[6] = g[6] + (dg - px + py - cxy);
-            o[7] = g[7] + (dg - px - py + cxy);
-            o[8] = g[8] + (dg + px - py - cxy);
-            if constexpr (is_half_<S>()) {
-                // encode with the reference density of the node that pulls each value
-                const R own = half_round(r);
+            for (int k = 0; k < 2; ++k) {
+                const R r = k == 0 ? rho0 : rho1;
+                if constexpr (is_half_<S>()) {
+                    // encode with the reference density of the node that pulls each value
+                    const R own = half_round(r);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const R dref = ((info >> opp_(i)) & 1u) ? own
-                                                           : half_round(sm.rho[k][ty + 2 + ey_(i)][tx + 2 + ex_(i)]);
-                    Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o[i], w_<R>(i) * dref);
+                    for (int i = 0; i < 9; ++i) {
+                        const R dref = ((info >> opp_(i)) & 1u) ? own
+                                                               : half_round(sm.rho[k][ty + 2 + ey_(i)][tx + 2 + ex_(i)]);
+                        Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o2[k][i], w_<R>(i) * dref);
+                    }
+                    static_cast<__half*>(a.rref_out)[k * a.plane + n] = __float2half_rn(float(r));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o2[k][i], R(0));
                 }
-                static_cast<__half*>(a.rref_out)[k * a.plane + n] = __float2half_rn(float(r));
-            } else {
+            }
+        } else {
+            const R uu3 = R(3) * (ux * ux + uy * uy);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o[i], R(0));
+            for (int k = 0; k < 2; ++k) {
+                const R* s = a.s[k];
+                const R r = k == 0 ? rho0 : rho1;
+                const R fx = k == 0 ? Fx0 : Fx1, fy = k == 0 ? Fy0 : Fy1;
+                const R* g = f[k];
+                const R d13 = g[1] - g[3], d24 = g[2] - g[4], d57 = g[5] - g[7], d86 = g[8] - g[6];
+                const R a13 = g[1] + g[3], a24 = g[2] + g[4], a57 = g[5] + g[7], a68 = g[6] + g[8];
+                const R sa = a13 + a24, sd = a57 + a68;
+                const R me = (R(2) * sd - sa) - R(4) * g[0];
+                const R mp = (sd - R(2) * sa) + R(4) * g[0];
+                const R mjx = d13 + (d57 + d86), mqx = (d57 + d86) - R(2) * d13;
+                const R mjy = d24 + (d57 - d86), mqy = (d57 - d86) - R(2) * d24;
+                const R mxx = a13 - a24, mxy = a57 - a68;
+                const R uF = ux * fx + uy * fy;
+                // post-collision moment increments: -s (m - m_eq) + (1 - s/2) F_m
+                const R de = -s[1] * (me - r * (uu3 - R(2))) + (R(1) - R(0.5) * s[1]) * (R(6) * uF);
+                const R dp = -s[2] * (mp - r * (R(1) - uu3)) + (R(1) - R(0.5) * s[2]) * (R(-6) * uF);
+                const R djx = -s[3] * (mjx - r * ux) + (R(1) - R(0.5) * s[3]) * fx;
+                const R dqx = -s[4] * (mqx + r * ux) - (R(1) - R(0.5) * s[4]) * fx;
+                const R djy = -s[5] * (mjy - r * uy) + (R(1) - R(0.5) * s[5]) * fy;
+                const R dqy = -s[6] * (mqy + r * uy) - (R(1) - R(0.5) * s[6]) * fy;
+                const R dxx = -s[7] * (mxx - r * (ux * ux - uy * uy)) +
+                              (R(1) - R(0.5) * s[7]) * (R(2) * (ux * fx - uy * fy));
+                const R dxy = -s[8] * (mxy - r * ux * uy) + (R(1) - R(0.5) * s[8]) * (ux * fy + uy * fx);
+                // back-transform T^-1 = T^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+                const R ce = de * R(1.0 / 36.0), cp = dp * R(1.0 / 36.0);
+                const R cjx = djx * R(1.0 / 6.0), cqx = dqx * R(1.0 / 12.0);
+                const R cjy = djy * R(1.0 / 6.0), cqy = dqy * R(1.0 / 12.0);
+                const R cxx = dxx * R(0.25), cxy = dxy * R(0.25);
+                const R ax_ = -ce - R(2) * cp, dg = R(2) * ce + cp;
+                const R bx = cjx - R(2) * cqx, by = cjy - R(2) * cqy;
+                const R px = cjx + cqx, py = cjy + cqy;
+                R o[9];
+                o[0] = g[0] + (R(4) * (cp - ce));
+                o[1] = g[1] + (ax_ + bx + cxx);
+                o[2] = g[2] + (ax_ + by - cxx);
+                o[3] = g[3] + (ax_ - bx + cxx);
+                o[4] = g[4] + (ax_ - by - cxx);
+                o[5] = g[5] + (dg + px + py + cxy);
+                o[6] = g[6] + (dg - px + py - cxy);
+                o[7] = g[7] + (dg - px - py + cxy);
+                o[8] = g[8] + (dg + px - py - cxy);
+                if constexpr (is_half_<S>()) {
+                    // encode with the reference density of the node that pulls each value
+                    const R own = half_round(r);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const R dref = ((info >> opp_(i)) & 1u) ? own
+                                                               : half_round(sm.rho[k][ty + 2 + ey_(i)][tx + 2 + ex_(i)]);
+                        Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o[i], w_<R>(i) * dref);
+                    }
+                    static_cast<__half*>(a.rref_out)[k * a.plane + n] = __float2half_rn(float(r));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o[i], R(0));
+                }
             }
         }
     }
