@@ -324,9 +324,29 @@ __device__ __forceinline__ bool site_rho(const D2Args<S, R>& a, int gx, int gy, 
     return true;
 }
 
+// (rho_1, rho_2) of one site, kept together so that a stencil tap is one
+// shared load and, in FP32, both components share packed FP32x2 FMAs.
+template <typename R>
+struct RhoPair;
+template <>
+struct RhoPair<float> {
+    using type = float2;
+};
+template <>
+struct RhoPair<double> {
+    using type = double2;
+};
+template <typename R>
+__device__ __forceinline__ typename RhoPair<R>::type rpair(R a, R b) {
+    typename RhoPair<R>::type v;
+    v.x = a;
+    v.y = b;
+    return v;
+}
+
 template <typename S, typename R, int TX, int TY>
 struct TileSmem {
-    R rho[2][TY + 4][TX + 4];
+    typename RhoPair<R>::type rr[TY + 4][TX + 4];
     unsigned char sol[TY + 4][TX + 4];
     R un[TX > TY ? TX : TY];
     R lam, chi;  // outlet coefficients of this step (general tiles that see the outlet)
@@ -393,8 +413,7 @@ __device__ __forceinline__ void stage_tile(const D2Args<S, R>& a, TileSmem<S, R,
             sol = 0;
         }
     }
-    sm.rho[0][ty + 2][tx + 2] = r0;
-    sm.rho[1][ty + 2][tx + 2] = r1;
+    sm.rr[ty + 2][tx + 2] = rpair<R>(r0, r1);
     sm.sol[ty + 2][tx + 2] = sol;
     // halo ring: densities only
     constexpr int RING = RX * RY - TX * TY;
@@ -414,8 +433,7 @@ __device__ __forceinline__ void stage_tile(const D2Args<S, R>& a, TileSmem<S, R,
         }
         R h0 = R(0), h1 = R(0);
         const bool ok = site_rho<S, R, MODE>(a, x0 - 2 + rx, y0 - 2 + ry, h0, h1);
-        sm.rho[0][ry][rx] = h0;
-        sm.rho[1][ry][rx] = h1;
+        sm.rr[ry][rx] = rpair<R>(h0, h1);
         sm.sol[ry][rx] = ok ? 0 : 1;
     };
     if (RING <= NT) {
@@ -594,8 +612,7 @@ __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSm
         pend_y = y;
         pend_rx = tx + 2;
         pend_ry = ty + 2;
-        sm.rho[0][ty + 2][tx + 2] = r0;
-        sm.rho[1][ty + 2][tx + 2] = r1;
+        sm.rr[ty + 2][tx + 2] = rpair<R>(r0, r1);
         sm.sol[ty + 2][tx + 2] = sol;
     } else if (tid < NT + RING) {
         // ---- halo ring: densities only ----
@@ -634,8 +651,7 @@ __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSm
                 }
             }
         }
-        sm.rho[0][ry][rx] = h0;
-        sm.rho[1][ry][rx] = h1;
+        sm.rr[ry][rx] = rpair<R>(h0, h1);
         sm.sol[ry][rx] = hs;
     } else if (tid >= G::SB) {
         // ---- face strips (and lambda, chi) ----
@@ -731,8 +747,7 @@ __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSm
                 r1 = rho_of(g[1]);
                 sol = 0;
             }
-            sm.rho[0][pend_ry][pend_rx] = r0;
-            sm.rho[1][pend_ry][pend_rx] = r1;
+            sm.rr[pend_ry][pend_rx] = rpair<R>(r0, r1);
             sm.sol[pend_ry][pend_rx] = sol;
         }
         __syncthreads();
@@ -743,12 +758,10 @@ __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSm
         for (int k = 0; k < 2; ++k)
 #pragma unroll
             for (int i = 0; i < 9; ++i) f[k][i] = sm.fs_f[own_strip][own_idx][k * 9 + i];
-        sm.rho[0][ty + 2][tx + 2] = rho_of(f[0]);
-        sm.rho[1][ty + 2][tx + 2] = rho_of(f[1]);
+        sm.rr[ty + 2][tx + 2] = rpair<R>(rho_of(f[0]), rho_of(f[1]));
     }
     if (def_j >= 0) {
-        sm.rho[0][def_ry][def_rx] = sm.fs_rho[def_j][def_e][0];
-        sm.rho[1][def_ry][def_rx] = sm.fs_rho[def_j][def_e][1];
+        sm.rr[def_ry][def_rx] = rpair<R>(sm.fs_rho[def_j][def_e][0], sm.fs_rho[def_j][def_e][1]);
     }
 }
 
@@ -862,31 +875,53 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
     // general tiles: the ring and strip warps are done once the tile is staged
     if (GEN && tid >= NT) return;
 
-    const R rho0 = sm.rho[0][ty + 2][tx + 2], rho1 = sm.rho[1][ty + 2][tx + 2];
+    const R rho0 = sm.rr[ty + 2][tx + 2].x, rho1 = sm.rr[ty + 2][tx + 2].y;
     R Fx0 = R(0), Fy0 = R(0), Fx1 = R(0), Fy1 = R(0);
     R ux = R(0), uy = R(0);
     const int own_face = (int)((info >> INFO_FACE_SHIFT) & 7u) - 1;
     const int nbr_face = (int)((info >> INFO_NBR_SHIFT) & 7u) - 1;
     if (fluid) {
         // ---- Eq. 10: 24-point 8th-order gradient of the other component ----
-        R g0x = R(0), g0y = R(0), g1x = R(0), g1y = R(0);
+        // opposite taps share the weight: sum over the half-plane before the
+        // centre of w e (psi(x + e) - psi(x - e)), both components at once
+        R g0x, g0y, g1x, g1y;
+        if constexpr (std::is_same<R, float>::value) {
+            float2 gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int dy = -2; dy <= 2; ++dy)
+            for (int dy = -2; dy <= 0; ++dy)
 #pragma unroll
-            for (int dx = -2; dx <= 2; ++dx) {
-                if (dx * dx + dy * dy == 0 || dx * dx + dy * dy > 8) continue;
-                const R w = w8_<R>(dx, dy);
-                const R p0 = sm.rho[0][ty + 2 + dy][tx + 2 + dx];
-                const R p1 = sm.rho[1][ty + 2 + dy][tx + 2 + dx];
-                if (dx != 0) {
-                    g0x += (w * R(dx)) * p0;
-                    g1x += (w * R(dx)) * p1;
+                for (int dx = -2; dx <= 2; ++dx) {
+                    if (dx * dx + dy * dy == 0 || dx * dx + dy * dy > 8 || (dy == 0 && dx > 0)) continue;
+                    const float w = w8_<float>(dx, dy);
+                    const float2 d = __ffma2_rn(sm.rr[ty + 2 - dy][tx + 2 - dx], make_float2(-1.f, -1.f),
+                                                sm.rr[ty + 2 + dy][tx + 2 + dx]);
+                    if (dx != 0) gx = __ffma2_rn(make_float2(w * dx, w * dx), d, gx);
+                    if (dy != 0) gy = __ffma2_rn(make_float2(w * dy, w * dy), d, gy);
                 }
-                if (dy != 0) {
-                    g0y += (w * R(dy)) * p0;
-                    g1y += (w * R(dy)) * p1;
+            g0x = gx.x;
+            g1x = gx.y;
+            g0y = gy.x;
+            g1y = gy.y;
+        } else {
+            g0x = g0y = g1x = g1y = R(0);
+#pragma unroll
+            for (int dy = -2; dy <= 0; ++dy)
+#pragma unroll
+                for (int dx = -2; dx <= 2; ++dx) {
+                    if (dx * dx + dy * dy == 0 || dx * dx + dy * dy > 8 || (dy == 0 && dx > 0)) continue;
+                    const R w = w8_<R>(dx, dy);
+                    const auto pp = sm.rr[ty + 2 + dy][tx + 2 + dx], mm = sm.rr[ty + 2 - dy][tx + 2 - dx];
+                    const R d0 = pp.x - mm.x, d1 = pp.y - mm.y;
+                    if (dx != 0) {
+                        g0x += (w * R(dx)) * d0;
+                        g1x += (w * R(dx)) * d1;
+                    }
+                    if (dy != 0) {
+                        g0y += (w * R(dy)) * d0;
+                        g1y += (w * R(dy)) * d1;
+                    }
                 }
-            }
+        }
         // ---- Eq. 11: adhesion, only in tiles that see a solid site ----
         R ax = R(0), ay = R(0);
         if (bflags & BLOCK_SOLID) {
@@ -979,7 +1014,7 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         const R dref = ((info >> opp_(i)) & 1u) ? own
-                                                               : half_round(sm.rho[k][ty + 2 + ey_(i)][tx + 2 + ex_(i)]);
+                                                               : half_round(k ? sm.rr[ty + 2 + ey_(i)][tx + 2 + ex_(i)].y : sm.rr[ty + 2 + ey_(i)][tx + 2 + ex_(i)].x);
                         Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o2[k][i], w_<R>(i) * dref);
                     }
                     static_cast<__half*>(a.rref_out)[k * a.plane + n] = __float2half_rn(float(r));
@@ -1039,7 +1074,7 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         const R dref = ((info >> opp_(i)) & 1u) ? own
-                                                               : half_round(sm.rho[k][ty + 2 + ey_(i)][tx + 2 + ex_(i)]);
+                                                               : half_round(k ? sm.rr[ty + 2 + ey_(i)][tx + 2 + ex_(i)].y : sm.rr[ty + 2 + ey_(i)][tx + 2 + ex_(i)].x);
                         Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o[i], w_<R>(i) * dref);
                     }
                     static_cast<__half*>(a.rref_out)[k * a.plane + n] = __float2half_rn(float(r));
