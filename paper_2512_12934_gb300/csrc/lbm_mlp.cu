@@ -347,12 +347,15 @@ __global__ void __launch_bounds__(NTB) mlp_infer_kernel(const float* __restrict_
         for (int q = threadIdx.x; q < H * H / 4; q += NTB) reinterpret_cast<float4*>(Wt)[q] = __ldg(src + q);
         __syncthreads();
         const float* bias = p + (l ? ob3 : ob2);
-        float acc[8][8];
+        // acc[r][c2] holds outputs (8 ng + 2 c2, 8 ng + 2 c2 + 1) of sample
+        // 8 sg + r: one packed FP32x2 FMA updates both (each lane rounds as
+        // fmaf does)
+        float2 acc[8][4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float bc = __ldg(bias + 8 * ng + c);
+        for (int c2 = 0; c2 < 4; ++c2) {
+            const float2 bc = make_float2(__ldg(bias + 8 * ng + 2 * c2), __ldg(bias + 8 * ng + 2 * c2 + 1));
 #pragma unroll
-            for (int r = 0; r < 8; ++r) acc[r][c] = bc;
+            for (int r = 0; r < 8; ++r) acc[r][c2] = bc;
         }
 #pragma unroll 2
         for (int k = 0; k < H; ++k) {
@@ -360,18 +363,24 @@ __global__ void __launch_bounds__(NTB) mlp_infer_kernel(const float* __restrict_
             const float4 w1 = reinterpret_cast<const float4*>(Wt + k * H + 8 * ng)[1];
             const float4 a0 = reinterpret_cast<const float4*>(in + k * TB + 8 * sg)[0];
             const float4 a1 = reinterpret_cast<const float4*>(in + k * TB + 8 * sg)[1];
-            const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            const float2 w[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
+                                 make_float2(w1.z, w1.w)};
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
-            for (int r = 0; r < 8; ++r)
+            for (int r = 0; r < 8; ++r) {
+                const float2 ar = make_float2(a[r], a[r]);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], w[c], acc[r][c]);
+                for (int c2 = 0; c2 < 4; ++c2) acc[r][c2] = __ffma2_rn(ar, w[c2], acc[r][c2]);
+            }
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            float4* o = reinterpret_cast<float4*>(out + (8 * ng + c) * TB + 8 * sg);
-            o[0] = make_float4(gelu(acc[0][c]), gelu(acc[1][c]), gelu(acc[2][c]), gelu(acc[3][c]));
-            o[1] = make_float4(gelu(acc[4][c]), gelu(acc[5][c]), gelu(acc[6][c]), gelu(acc[7][c]));
+        for (int c2 = 0; c2 < 4; ++c2) {
+            float4* o0 = reinterpret_cast<float4*>(out + (8 * ng + 2 * c2) * TB + 8 * sg);
+            float4* o1 = reinterpret_cast<float4*>(out + (8 * ng + 2 * c2 + 1) * TB + 8 * sg);
+            o0[0] = make_float4(gelu(acc[0][c2].x), gelu(acc[1][c2].x), gelu(acc[2][c2].x), gelu(acc[3][c2].x));
+            o0[1] = make_float4(gelu(acc[4][c2].x), gelu(acc[5][c2].x), gelu(acc[6][c2].x), gelu(acc[7][c2].x));
+            o1[0] = make_float4(gelu(acc[0][c2].y), gelu(acc[1][c2].y), gelu(acc[2][c2].y), gelu(acc[3][c2].y));
+            o1[1] = make_float4(gelu(acc[4][c2].y), gelu(acc[5][c2].y), gelu(acc[6][c2].y), gelu(acc[7][c2].y));
         }
         float* t = in;
         in = out;
