@@ -765,6 +765,154 @@ __device__ __forceinline__ void stage_tile_general(const D2Args<S, R>& a, TileSm
     }
 }
 
+// Serial staging of a general tile by its NT node threads (strips, own
+// node, halo ring in turn).  Used when the general list is long enough to
+// fill the GPU by itself (batched ensembles): there the extra staging warps
+// of GenRoles cost more SM room than their latency saving is worth.
+template <typename S, typename R, int TX, int TY>
+__device__ __forceinline__ void stage_tile_compact(const D2Args<S, R>& a, TileSmemGen<S, R, TX, TY>& sm, int x0,
+                                                   int y0, int tx, int ty, unsigned strips, unsigned bflags,
+                                                   R (&f)[2][9], unsigned& info, bool& fluid) {
+    constexpr int RX = TX + 4, RY = TY + 4, NT = TX * TY;
+    constexpr int RING = RX * RY - TX * TY;
+    const int tid = threadIdx.x;
+    // ---- lambda (Eq. 21) and chi (Eq. 23): the last warp folds the previous
+    // step's partials (same order, same bits as the staging-role tiles)
+    if (bflags & BLOCK_LAMBDA) {
+        if (tid >= NT - 32) {
+            LamFold L;
+            fold_begin(a, L);
+            double dl, dc;
+            fold_finish(a, L, dl, dc);
+            if (tid == NT - 32) {
+                sm.lam = R(dl);
+                sm.chi = R(dc);
+            }
+        }
+        __syncthreads();
+    }
+    const R lam = (bflags & BLOCK_LAMBDA) ? sm.lam : R(0);
+    const int side0 = (int)(strips & 0xffu) - 1, side1 = (int)((strips >> 8) & 0xffu) - 1;
+    const int len0 = side0 < 0 ? 0 : (side0 <= 1 ? RY : RX);
+    const int len1 = side1 < 0 ? 0 : (side1 <= 1 ? RY : RX);
+    auto strip_of = [&](int side) { return side == side0 ? 0 : (side == side1 ? 1 : -1); };
+
+    // ---- phase 0: face strips ----
+    {
+        const int base = RING <= NT ? RING : 0;
+        for (int t = tid - base; t >= 0 && t < len0 + len1; t += NT) {
+            const int j = t < len0 ? 0 : 1;
+            const int e = j == 0 ? t : t - len0;
+            const int side = j == 0 ? side0 : side1;
+            int sx, sy;
+            strip_node<TX, TY>(side, e, x0, y0, a.nx, a.ny, sx, sy);
+            if (sx < 0 || sx >= a.nx || sy < 0 || sy >= a.ny) continue;
+            const unsigned inf = a.info[sy * a.pitch + sx];
+            if ((inf & INFO_SOLID) || !((inf >> INFO_FACE_SHIFT) & 7u)) continue;
+            R g[2][9];
+            pull_general(a, sx, sy, inf, lam, g);
+            sm.fs_rho[j][e][0] = rho_of(g[0]);
+            sm.fs_rho[j][e][1] = rho_of(g[1]);
+            const int o = side <= 1 ? sy - y0 : sx - x0;
+            const bool own = sx >= x0 && sx < x0 + TX && sy >= y0 && sy < y0 + TY;
+            if (own)
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) sm.fs_f[j][o][k * 9 + i] = g[k][i];
+        }
+    }
+
+    // ---- own node ----
+    const int x = x0 + tx, y = y0 + ty;
+    const bool inb = (x >= 0 && x < a.nx && y >= 0 && y < a.ny);
+    info = INFO_SOLID;
+    fluid = false;
+    int own_strip = -1, own_idx = 0;
+    R r0 = R(0), r1 = R(0);
+    unsigned char sol = 1;
+    if (inb) {
+        info = a.info[y * a.pitch + x];
+        fluid = !(info & INFO_SOLID);
+        if (fluid) {
+            const int fid = (int)((info >> INFO_FACE_SHIFT) & 7u);
+            if (fid) {
+                const int side = a.face[fid - 1].side;
+                own_strip = strip_of(side);
+                own_idx = side <= 1 ? ty : tx;
+            }
+            if (own_strip < 0) {
+                pull_general(a, x, y, info, lam, f);
+                r0 = rho_of(f[0]);
+                r1 = rho_of(f[1]);
+            }
+            sol = 0;
+        }
+    } else if (site_rho<S, R, 2>(a, x, y, r0, r1, lam)) {
+        sol = 0;
+    }
+    sm.rr[ty + 2][tx + 2] = rpair<R>(r0, r1);
+    sm.sol[ty + 2][tx + 2] = sol;
+
+    // ---- halo ring ----
+    int def_j = -1, def_e = 0, def_rx = 0, def_ry = 0;
+    for (int p = tid; p < RING; p += NT) {
+        int rx, ry;
+        if (p < 2 * RX) {
+            ry = p / RX;
+            rx = p % RX;
+        } else if (p < 4 * RX) {
+            ry = TY + 2 + (p - 2 * RX) / RX;
+            rx = (p - 2 * RX) % RX;
+        } else {
+            const int q = p - 4 * RX;
+            ry = 2 + q / 4;
+            const int c = q % 4;
+            rx = c < 2 ? c : TX + c;
+        }
+        int gx = x0 - 2 + rx, gy = y0 - 2 + ry;
+        R h0 = R(0), h1 = R(0);
+        unsigned char hs = 1;
+        if (!resolve_site(a, gx, gy)) {
+            const unsigned inf = a.info[gy * a.pitch + gx];
+            if (!(inf & INFO_SOLID)) {
+                hs = 0;
+                const int fid = (int)((inf >> INFO_FACE_SHIFT) & 7u);
+                int j = -1, e = -1;
+                if (fid) {
+                    const int side = a.face[fid - 1].side;
+                    j = strip_of(side);
+                    if (j >= 0) e = strip_entry<TX, TY>(side, gx, gy, x0, y0, a.nx, a.ny);
+                }
+                if (j >= 0 && e >= 0 && RING <= NT) {
+                    def_j = j;  // filled from the strip after the barrier
+                    def_e = e;
+                    def_rx = rx;
+                    def_ry = ry;
+                } else {
+                    R g[2][9];
+                    pull_general(a, gx, gy, inf, lam, g);
+                    h0 = rho_of(g[0]);
+                    h1 = rho_of(g[1]);
+                }
+            }
+        }
+        sm.rr[ry][rx] = rpair<R>(h0, h1);
+        sm.sol[ry][rx] = hs;
+    }
+    __syncthreads();
+    if (own_strip >= 0) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[k][i] = sm.fs_f[own_strip][own_idx][k * 9 + i];
+        sm.rr[ty + 2][tx + 2] = rpair<R>(rho_of(f[0]), rho_of(f[1]));
+    }
+    if (def_j >= 0) {
+        sm.rr[def_ry][def_rx] = rpair<R>(sm.fs_rho[def_j][def_e][0], sm.fs_rho[def_j][def_e][1]);
+    }
+}
+
 // Eq. 1 for both components of one node in moment space (T of Eq. 3, S of
 // Eq. 4), delta form: post-collision moment increments -s (m - m_eq) +
 // (1 - s/2) F_m, back-transformed with T^-1 = T^T diag(1/9, 1/36, 1/36, 1/6,
@@ -851,7 +999,7 @@ __device__ __forceinline__ void collide_pair(const A& a, const float (&f)[2][9],
 
 // One tile of one step.  bxy = bx | by << 16; bflags = BLOCK_* flags; strips
 // and slot are used by general tiles only.
-template <typename S, typename R, int TX, int TY, bool GEN>
+template <typename S, typename R, int TX, int TY, bool GEN, bool ROLES = true>
 __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsigned bflags, unsigned strips,
                                           int slot) {
     constexpr int NT = TX * TY, NW = NT / 32;
@@ -867,8 +1015,10 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
     R f[2][9];
     unsigned info;
     bool fluid;
-    if constexpr (GEN)
+    if constexpr (GEN && ROLES)
         stage_tile_general<S, R, TX, TY>(a, smx, x0, y0, strips, bflags, f, info, fluid);
+    else if constexpr (GEN)
+        stage_tile_compact<S, R, TX, TY>(a, smx, x0, y0, tx, ty, strips, bflags, f, info, fluid);
     else if (bflags & BLOCK_EDGE) stage_tile<S, R, TX, TY, 1>(a, sm, x0, y0, tx, ty, f, info, fluid);
     else stage_tile<S, R, TX, TY, 0>(a, sm, x0, y0, tx, ty, f, info, fluid);
     __syncthreads();
@@ -1141,9 +1291,14 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
 // variant.  FP32 keeps 80 (measured on GB300: a 64-register cap spilled
 // ~0.5 KB per thread and made the step 20 % slower, although it would leave
 // room for a fifth fast tile on the SM).
-template <typename R, int TX, int TY>
+template <int TX, int TY, bool ROLES>
+__host__ __device__ constexpr int gen_threads() {
+    return ROLES ? GenRoles<TX, TY>::THREADS : TX * TY;
+}
+
+template <typename R, int TX, int TY, bool ROLES>
 __host__ __device__ constexpr int gen_maxreg() {
-    constexpr int fit = 65536 / GenRoles<TX, TY>::THREADS / 8 * 8;
+    constexpr int fit = 65536 / gen_threads<TX, TY, ROLES>() / 8 * 8;
     constexpr int want = sizeof(R) == 4 ? 80 : 128;
     return want < fit ? want : fit;
 }
@@ -1156,10 +1311,10 @@ __global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constan
     step_tile<S, R, TX, TY, false>(a, a.blocks[li], a.block_flags[li], 0u, -1);
 }
 
-template <typename S, typename R, int TX, int TY>
-__global__ void __maxnreg__((gen_maxreg<R, TX, TY>())) d2q9_general_kernel(const __grid_constant__ D2Args<S, R> a) {
+template <typename S, typename R, int TX, int TY, bool ROLES>
+__global__ void __maxnreg__((gen_maxreg<R, TX, TY, ROLES>())) d2q9_general_kernel(const __grid_constant__ D2Args<S, R> a) {
     const int li = a.list_off + blockIdx.x;
-    step_tile<S, R, TX, TY, true>(a, a.blocks[li], a.block_flags[li], a.block_strips[li], a.block_slot[li]);
+    step_tile<S, R, TX, TY, true, ROLES>(a, a.blocks[li], a.block_flags[li], a.block_strips[li], a.block_slot[li]);
 }
 
 // Batched step: the list interleaves the tiles of many instances; each CTA
@@ -1168,7 +1323,7 @@ __global__ void __maxnreg__((gen_maxreg<R, TX, TY>())) d2q9_general_kernel(const
 // Batched step: the list interleaves the tiles of many instances; each CTA
 // copies its instance's arguments into shared memory and runs the same tile
 // code, so a batch step equals stepping every member on its own.
-template <typename S, typename R, int TX, int TY, bool GEN>
+template <typename S, typename R, int TX, int TY, bool GEN, bool ROLES = true>
 __device__ __forceinline__ void batch_tile(const BatchArgs<S, R>& b) {
     __shared__ D2Args<S, R> sa;
     const int li = b.off + blockIdx.x;
@@ -1180,7 +1335,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<S, R>& b) {
         for (int i = threadIdx.x; i < (int)(sizeof(D2Args<S, R>) / 4); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    step_tile<S, R, TX, TY, GEN>(sa, b.blocks[li], b.flags[li], b.strips[li], b.slot[li]);
+    step_tile<S, R, TX, TY, GEN, ROLES>(sa, b.blocks[li], b.flags[li], b.strips[li], b.slot[li]);
 }
 
 template <typename S, typename R, int TX, int TY>
@@ -1188,9 +1343,9 @@ __global__ void __launch_bounds__(TX * TY) d2q9_batch_kernel(const __grid_consta
     batch_tile<S, R, TX, TY, false>(b);
 }
 
-template <typename S, typename R, int TX, int TY>
-__global__ void __maxnreg__((gen_maxreg<R, TX, TY>())) d2q9_batch_general_kernel(const __grid_constant__ BatchArgs<S, R> b) {
-    batch_tile<S, R, TX, TY, true>(b);
+template <typename S, typename R, int TX, int TY, bool ROLES>
+__global__ void __maxnreg__((gen_maxreg<R, TX, TY, ROLES>())) d2q9_batch_general_kernel(const __grid_constant__ BatchArgs<S, R> b) {
+    batch_tile<S, R, TX, TY, true, ROLES>(b);
 }
 
 // FP64 mass / speed reduction for diagnostics.
@@ -1271,16 +1426,50 @@ void d2q9_variant_tile(int variant, int* tx, int* ty) {
 }
 int d2q9_num_variants() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
 
+// A general list of at most two CTAs per SM is latency-bound: its tiles stage
+// with the extra GenRoles warps.  Longer lists (batched ensembles) fill the
+// GPU by themselves and stage serially on the node threads.
+static bool general_roles(int nblocks) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    return nblocks <= 2 * sms;
+}
+
+// (Serial staging is built for FP32 storage only, to bound compile time;
+// the other precisions always stage with GenRoles.)
 template <typename S, typename R, int TX, int TY>
 static void launch_tile(const D2Args<S, R>& a, bool general, int nblocks, cudaStream_t st) {
-    if (general) d2q9_general_kernel<S, R, TX, TY><<<nblocks, GenRoles<TX, TY>::THREADS, 0, st>>>(a);
-    else d2q9_step_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(a);
+    if (!general) {
+        d2q9_step_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(a);
+        return;
+    }
+    if constexpr (std::is_same<S, float>::value) {
+        if (!general_roles(nblocks)) {
+            d2q9_general_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(a);
+            return;
+        }
+    }
+    d2q9_general_kernel<S, R, TX, TY, true><<<nblocks, GenRoles<TX, TY>::THREADS, 0, st>>>(a);
 }
 
 template <typename S, typename R, int TX, int TY>
 static void launch_batch_tile(const BatchArgs<S, R>& b, bool general, int nblocks, cudaStream_t st) {
-    if (general) d2q9_batch_general_kernel<S, R, TX, TY><<<nblocks, GenRoles<TX, TY>::THREADS, 0, st>>>(b);
-    else d2q9_batch_kernel<S, R, TX, TY><<<nblocks, TX * TY, 0, st>>>(b);
+    if (!general) {
+        d2q9_batch_kernel<S, R, TX, TY><<<nblocks, TX * TY, 0, st>>>(b);
+        return;
+    }
+    if constexpr (std::is_same<S, float>::value) {
+        if (!general_roles(nblocks)) {
+            d2q9_batch_general_kernel<S, R, TX, TY, false><<<nblocks, TX * TY, 0, st>>>(b);
+            return;
+        }
+    }
+    d2q9_batch_general_kernel<S, R, TX, TY, true><<<nblocks, GenRoles<TX, TY>::THREADS, 0, st>>>(b);
 }
 
 template <typename S, typename R>
