@@ -36,7 +36,7 @@ typedef enum {
     LBM_ERR_OOM = 3,         /* device or host allocation failed */
     LBM_ERR_DIVERGED = 4,    /* a non-finite density or velocity appeared */
     LBM_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
-    LBM_ERR_UNSUPPORTED = 6, /* valid request this build does not implement */
+    LBM_ERR_UNSUPPORTED = 6, /* valid request this library does not implement */
     LBM_ERR_IO = 7           /* checkpoint file could not be read/written */
 } lbm_status;
 

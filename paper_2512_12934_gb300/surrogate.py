@@ -10,7 +10,7 @@ L/W_c = 1 + alpha * Q_d/Q_c.  This module learns the map
 this solver, with a 5-member MLP ensemble trained and evaluated by the
 library's own kernels (lbm.MLP).  The plain solver stays the fallback for
 every query whose ensemble spread exceeds a tolerance (5 % by default) or
-that lies outside the training box, and it is the judge of the surrogate's
+that lies outside the training box, and it is the reference for the surrogate's
 error.
 
 Everything here is host-side orchestration: solver runs go through

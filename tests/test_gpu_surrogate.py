@@ -1,7 +1,7 @@
 """The learned surrogate end to end: solver-generated T-junction labels,
 ensemble training in the library's MLP kernels, and queries answered by the
 network where its ensemble spread is within 5 % and by the solver elsewhere.
-The solver is the judge: held-out points are compared with their solver
+The solver is the reference: held-out points are compared with their solver
 labels, and fallback answers must equal the solver's bit for bit."""
 import time
 
