@@ -711,6 +711,18 @@ void orc_set_f(orc_state* st, const double* f) {
     memcpy(st->f, f, sizeof(double) * NCOMP * NQ * (size_t)st->N);
 }
 
+/* Overwrite the post-stream, post-boundary populations of the last step
+ * (the f_i(x_N, t) that Eq. 20 reads in the next step), [2][9][N]. */
+void orc_set_fpost(orc_state* st, const double* f) {
+    memcpy(st->fpost, f, sizeof(double) * NCOMP * NQ * (size_t)st->N);
+}
+
+/* Overwrite lambda (Eq. 21) and chi (Eq. 23) that the next step uses. */
+void orc_set_outlet_coeffs(orc_state* st, double lambda, double chi) {
+    st->lambda = lambda;
+    st->chi = chi;
+}
+
 /* Post-stream, post-boundary populations of the last step, [2][9][N]. */
 void orc_get_fpost(const orc_state* st, double* f) {
     memcpy(f, st->fpost, sizeof(double) * NCOMP * NQ * (size_t)st->N);

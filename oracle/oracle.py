@@ -94,9 +94,11 @@ def lib():
         L.orc_destroy.argtypes = [ctypes.c_void_p]
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
-        for name in ("orc_get_f", "orc_set_f", "orc_get_fpost", "orc_get_force_prev", "orc_get_scalars"):
+        for name in ("orc_get_f", "orc_set_f", "orc_get_fpost", "orc_set_fpost", "orc_get_force_prev",
+                     "orc_get_scalars"):
             getattr(L, name).argtypes = [ctypes.c_void_p, _dp]
         L.orc_get_macros.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+        L.orc_set_outlet_coeffs.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
         L.orc_eval_forces.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.orc_feq.argtypes = [ctypes.c_double] * 3 + [_dp]
         L.orc_fbar.argtypes = [ctypes.c_double] * 4 + [_dp]
@@ -257,6 +259,16 @@ class Oracle2D:
         out = np.zeros(18 * self.N)
         lib().orc_get_fpost(self.h, _ptr(out))
         return out.reshape(2, 9, self.ny, self.nx)
+
+    def set_fpost(self, f):
+        """Replace the last step's post-boundary populations (the f(x_N, t)
+        that the next step's Eq. 20 reads)."""
+        a = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        lib().orc_set_fpost(self.h, _ptr(a))
+
+    def set_outlet_coeffs(self, lam, chi):
+        """Replace lambda and chi that the next step uses."""
+        lib().orc_set_outlet_coeffs(self.h, float(lam), float(chi))
 
     def force_prev(self):
         out = np.zeros(4 * self.N)

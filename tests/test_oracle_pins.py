@@ -412,6 +412,171 @@ def test_inlet_alpha_restores_prescribed_momentum():
             assert abs(mx - tx) < 1e-15 and abs(my) < 1e-15
 
 
+def test_inlet_alpha_restores_prescribed_momentum_on_a_y_face():
+    """Eq. 14 (a face normal to y, unknowns 4, 7, 8) with the alpha
+    correction of Eqs. 15-19: every node of the T-junction's top inlet
+    carries exactly rho_in,k u_in, where u_in points along -y."""
+    w = W.tjunction(Wc=12, length_factor=8, Wd=6, side_len=10, x_side=20, q_ratio=0.8, M=1.0,
+                    G12=1.2, u_c=0.02)
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u)
+    o.step(30)
+    ex, ey, _, _ = O.lattice()
+    fp = o.fpost()
+    Fp = o.force_prev()
+    face = w.cfg["faces"][1]
+    assert face["side"] == "ymax"
+    yt = w.cfg["ny"] - 1
+    worst = 0.0
+    for k in range(2):
+        for x in range(face["lo"], face["hi"] + 1):
+            mx = (ex * fp[k, :, yt, x]).sum() + 0.5 * Fp[k, 0, yt, x]
+            my = (ey * fp[k, :, yt, x]).sum() + 0.5 * Fp[k, 1, yt, x]
+            ty = -face["rho_in"][k] * face["profile"][x - face["lo"]]
+            worst = max(worst, abs(mx), abs(my - ty))
+    assert worst < 1e-15
+    # without the correction the y-face misses the prescribed momentum
+    cfg = dict(w.cfg, faces=[dict(f, alpha=0) if f["side"] == "ymax" else f for f in w.cfg["faces"]])
+    o2 = O.Oracle2D(cfg, w.solid, w.rho, w.u)
+    o2.step(30)
+    fp2, Fp2 = o2.fpost(), o2.force_prev()
+    miss = max(abs((ey * fp2[0, :, yt, x]).sum() + 0.5 * Fp2[0, 1, yt, x]
+                   + face["rho_in"][0] * face["profile"][x - face["lo"]])
+               for x in range(face["lo"], face["hi"] + 1))
+    assert miss > 1e-6
+
+
+def test_outlet_update_advects_a_linear_signal_exactly():
+    """Eq. 20 is the implicit upwind form of df/dt + lambda df/dx = 0 at
+    x_N.  A signal linear in x and carried at speed lambda,
+    f = a + b (x - lambda t), satisfies it exactly, so the oracle must give
+    a + b (N - lambda (t + 1)) at x_N from f(x_N, t) = a + b (N - lambda t)
+    and f(x_{N-1}, t + 1) = a + b (N - 1 - lambda (t + 1)).  The check fails
+    if the weights 1 and lambda trade places, if f(x_N) is taken at t + 1
+    instead of t, or if another lambda than the one set for the step is
+    used.  Collisionless and force-free (S = 0, G12 = 0), so the streamed
+    value at x_{N-1} is the one written at x_N."""
+    nx, ny = 9, 6
+    cfg = W._base_cfg(nx, ny, (0, 1), 0.0, (0.0, 0.0), (1 / 6, 1 / 6))
+    cfg["s_full"] = [[0.0] * 9, [0.0] * 9]
+    cfg["faces"] = [{"kind": "outlet", "side": "xmax", "lo": 0, "hi": ny - 1, "rho_in": (0.0, 0.0),
+                     "alpha": 0, "chi": 1, "profile": np.zeros(ny)}]
+    o = O.Oracle2D(cfg, None, np.ones((2, ny, nx)), np.zeros((2, ny, nx)))
+    rng = np.random.default_rng(20)
+    f = rng.uniform(0.05, 0.2, (2, 9, ny, nx))
+    fprev = rng.uniform(0.05, 0.2, (2, 9, ny, nx))
+    N = nx - 1
+    lam, t = 0.37, 5.0
+    a = rng.uniform(0.1, 0.2, (2, 9))
+    b = rng.uniform(0.01, 0.02, (2, 9))
+    unknown = (3, 6, 7)
+    for k in range(2):
+        for i in unknown:
+            # the pull of direction i at x_{N-1} reads x_N (rows wrap; the signal is row-independent)
+            f[k, i, :, N] = a[k, i] + b[k, i] * (N - 1 - lam * (t + 1))
+            fprev[k, i, :, N] = a[k, i] + b[k, i] * (N - lam * t)
+    o.set_f(f)
+    o.set_fpost(fprev)
+    o.set_outlet_coeffs(lam, 1.0)
+    o.step(1)
+    got = o.fpost()
+    for k in range(2):
+        for i in unknown:
+            want = a[k, i] + b[k, i] * (N - lam * (t + 1))
+            assert np.max(np.abs(got[k, i, :, N] - want)) < 1e-15
+            # the same update with the weights swapped would miss by b (1 - lam) (1 + lam) / (1 + lam)
+            swapped = (lam * fprev[k, i, 0, N] + f[k, i, 0, N]) / (1 + lam)
+            assert abs(swapped - want) > 1e-3
+
+
+def test_outlet_lambda_is_the_mean_normal_speed_of_the_column_before_the_outlet():
+    """Eq. 21: lambda is the mean normal velocity over the fluid nodes of
+    x_{N-1}.  In a uniform stream of speed U through a velocity inlet and a
+    convective outlet (periodic across), every node keeps U exactly, so
+    lambda = U and, with equal inflow and outflow, chi = 1 (Eq. 23)."""
+    nx, ny, U = 12, 7, 0.031
+    cfg = W._base_cfg(nx, ny, (0, 1), 0.0, (0.0, 0.0), (0.1, 0.1))
+    cfg["faces"] = [
+        {"kind": "inlet", "side": "xmin", "lo": 0, "hi": ny - 1, "rho_in": (0.3, 0.9), "alpha": 1, "chi": 0,
+         "profile": np.full(ny, U)},
+        {"kind": "outlet", "side": "xmax", "lo": 0, "hi": ny - 1, "rho_in": (0.0, 0.0), "alpha": 0, "chi": 1,
+         "profile": np.zeros(ny)}]
+    rho = np.empty((2, ny, nx))
+    rho[0], rho[1] = 0.3, 0.9
+    u = np.zeros((2, ny, nx))
+    u[0] = U
+    o = O.Oracle2D(cfg, None, rho, u)
+    o.step(40)
+    s = o.scalars()
+    r, uu, _ = o.macros()
+    assert abs(s["lambda"] - U) < 1e-15
+    assert abs(s["chi"] - 1.0) < 1e-13
+    assert np.max(np.abs(uu[0] - U)) < 1e-15 and np.max(np.abs(uu[1])) < 1e-15
+    assert np.max(np.abs(r - rho)) < 1e-14
+
+
+def _forces_with_explicit_ghosts(psi, solid, G12, Gw, open_x, order=(0, 1)):
+    """Eqs. 10 and 11 evaluated on an array padded by two explicit ghost
+    columns per open side, filled as Eqs. 24 and 25 prescribe (the first
+    ghost takes the density of the boundary node x1, the second that of
+    x2; `order` = (1, 0) swaps them); closed edges are solid.  An
+    independent restatement of what the oracle does by index mirroring."""
+    g = golden()
+    wmap = {int(a): float(Fraction(b)) for a, b in (t.split(":") for t in g["w8"].split())}
+    taps = [(dx, dy, wmap[dx * dx + dy * dy]) for dy in range(-2, 3) for dx in range(-2, 3)
+            if dx * dx + dy * dy in wmap]
+    ny, nx = solid.shape
+    P = np.zeros((2, ny + 4, nx + 4))
+    Sd = np.ones((ny + 4, nx + 4))          # solid indicator, 1 outside closed edges
+    P[:, 2:ny + 2, 2:nx + 2] = psi * (solid == 0)
+    Sd[2:ny + 2, 2:nx + 2] = solid != 0
+    g1, g2 = order
+    if open_x[0]:   # ghost x = -1 <- column x1 (index 0), x = -2 <- x2 (index 1)
+        P[:, 2:ny + 2, 1], P[:, 2:ny + 2, 0] = P[:, 2:ny + 2, 2 + g1], P[:, 2:ny + 2, 2 + g2]
+        Sd[2:ny + 2, 1], Sd[2:ny + 2, 0] = Sd[2:ny + 2, 2 + g1], Sd[2:ny + 2, 2 + g2]
+    if open_x[1]:   # ghost x = nx <- x_N (index nx-1), x = nx+1 <- x_{N-1}
+        P[:, 2:ny + 2, nx + 2], P[:, 2:ny + 2, nx + 3] = P[:, 2:ny + 2, nx + 1 - g1], P[:, 2:ny + 2, nx + 1 - g2]
+        Sd[2:ny + 2, nx + 2], Sd[2:ny + 2, nx + 3] = Sd[2:ny + 2, nx + 1 - g1], Sd[2:ny + 2, nx + 1 - g2]
+    F = np.zeros((2, 2, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            if solid[y, x]:
+                continue
+            gsum = np.zeros((2, 2))
+            asum = np.zeros(2)
+            for dx, dy, wt in taps:
+                gsum[:, 0] += wt * P[:, y + 2 + dy, x + 2 + dx] * dx
+                gsum[:, 1] += wt * P[:, y + 2 + dy, x + 2 + dx] * dy
+                asum += wt * Sd[y + 2 + dy, x + 2 + dx] * np.array([dx, dy])
+            for k in range(2):
+                F[k, :, y, x] = -G12 * psi[k, y, x] * gsum[1 - k] - Gw[k] * psi[k, y, x] * asum
+    return F
+
+
+def test_ghost_layers_mirror_the_two_boundary_columns():
+    """Eqs. 24, 25: the forces near both open faces equal the stencil sums
+    over two explicit ghost columns that copy rho(x1), rho(x2) at the inlet
+    and rho(x_N), rho(x_{N-1}) at the outlet.  The densities of x1 and x2
+    differ everywhere, so mirroring onto the wrong column, or reading zero
+    there, changes the force at every node of the first two columns."""
+    w = _small_channel()
+    o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u)
+    rng = np.random.default_rng(24)
+    ny, nx = w.solid.shape
+    psi = rng.uniform(0.1, 1.0, (2, ny, nx))
+    psi[:, :, 1] += 0.5                      # x2 differs from x1 by far more than the noise
+    psi[:, :, nx - 2] += 0.5
+    psi[:, w.solid != 0] = 0.0
+    Fo = o.eval_forces(psi)
+    Fh = _forces_with_explicit_ghosts(psi, w.solid, w.cfg["G12"], w.cfg["Gw"], (True, True))
+    assert np.max(np.abs(Fo - Fh)) < 1e-14
+    # the check can see a wrong mirror: swapped ghosts, or ghosts read as solid
+    Fs = _forces_with_explicit_ghosts(psi, w.solid, w.cfg["G12"], w.cfg["Gw"], (True, True), order=(1, 0))
+    Fc = _forces_with_explicit_ghosts(psi, w.solid, w.cfg["G12"], w.cfg["Gw"], (False, False))
+    for Fx in (Fs, Fc):
+        assert np.max(np.abs(Fx[:, :, :, :2] - Fo[:, :, :, :2])) > 1e-3
+        assert np.max(np.abs(Fx[:, :, :, -2:] - Fo[:, :, :, -2:])) > 1e-3
+
+
 def test_inlet_without_alpha_misses_prescribed_momentum():
     w = _small_channel(alpha=False)
     o = O.Oracle2D(w.cfg, w.solid, w.rho, w.u)
