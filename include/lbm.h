@@ -57,6 +57,9 @@ enum { LBM_XMIN = 0, LBM_XMAX = 1, LBM_YMIN = 2, LBM_YMAX = 3, LBM_ZMIN = 4, LBM
  * the largest viscosity of the two phases (Sec. III A of the paper). */
 enum { LBM_SEPS_OWN_NU = 0, LBM_SEPS_MAX_NU = 1 };
 
+/* Step schedules (lbm_set_schedule, lbm_batch_set_schedule). */
+enum { LBM_SCHEDULE_GRAPHS = 0, LBM_SCHEDULE_PERSISTENT = 1 };
+
 typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
 
 /* Lattice and grid.  nz = 1 for D2Q9.  Every non-periodic extent must be
@@ -226,6 +229,13 @@ lbm_status lbm_tile_stats(lbm_ctx* ctx, int* variant, int* fast_tiles, int* gene
  * first use); 0 launches every step individually.  Results are identical. */
 lbm_status lbm_set_graph_mode(lbm_ctx* ctx, int use_graphs);
 
+/* Schedule of lbm_step for this context: LBM_SCHEDULE_GRAPHS (default) or
+ * LBM_SCHEDULE_PERSISTENT (FP32 storage only; see lbm_batch_set_schedule,
+ * of which this is the one-member case).  Under the persistent schedule
+ * lbm_sync also reports LBM_ERR_TIMEOUT, and lbm_enable_kernel_timing takes
+ * no samples.  Waits for the context's stream first. */
+lbm_status lbm_set_schedule(lbm_ctx* ctx, int schedule);
+
 /* FP64 mass of each component of caller-owned D2Q9 populations, for callers
  * that cannot allocate device memory (a process whose device memory is all
  * owned by another allocator or arena).  The paper has no counterpart: this
@@ -240,9 +250,16 @@ lbm_status lbm_set_graph_mode(lbm_ctx* ctx, int use_graphs);
  * doubles (1 MiB) that every GPU loading this library keeps until process
  * exit; ny > 65536 is rejected with LBM_ERR_INVALID_ARG.  Every call on a
  * device reuses that array, so calls that overlap on the GPU (concurrent
- * streams or host threads) race and give wrong sums; serialise them.  The
- * first call on each device (with that device current) resolves the
- * array's device address: make that first call before any stream capture.
+ * streams or host threads) race and give wrong sums; serialise them.  Each
+ * call outside a stream capture resolves the array's device address in the
+ * current context (so the address stays valid across cudaDeviceReset); a
+ * call inside a capture reuses the address resolved by the last call on
+ * that device outside a capture, so make one call on each device before
+ * capturing (a capture with no earlier call fails with
+ * LBM_ERR_INVALID_ARG), and do not reset the device between that call and
+ * the capture.  If a CUDA error from earlier work is pending on the calling
+ * thread the call launches nothing and returns LBM_ERR_CUDA, leaving that
+ * error in place for its owner.
  * Returns without waiting; the result is ready when the stream reaches it. */
 lbm_status lbm_mass_noalloc(const void* f, int precision, int nx, int ny, int pitch,
                             const uint8_t* solid, double* mass, void* cuda_stream);
@@ -286,6 +303,36 @@ lbm_status lbm_batch_info(lbm_batch* b, int* variant, int* fast_tiles, int* gene
 
 /* CUDA-graph replay on (default) or off for batch steps. */
 lbm_status lbm_batch_set_graph_mode(lbm_batch* b, int use_graphs);
+
+/* How a batch step call runs on the GPU.
+ *  LBM_SCHEDULE_GRAPHS (default): per time step, one launch for the fast
+ *    tile list and one for the general list, replayed from captured CUDA
+ *    graphs in runs of 32 steps.
+ *  LBM_SCHEDULE_PERSISTENT (FP32 storage only): one cooperative launch per
+ *    run of up to 1024 steps.  Its CTAs (as many as fit on the GPU at once,
+ *    at most one per tile) walk the concatenated tile descriptors of all
+ *    members in every step and meet at a grid-wide barrier between steps;
+ *    each wait at that barrier is bounded (about one second of SM clock by
+ *    default), and a wait that runs out ends the launch: lbm_batch_sync then
+ *    returns LBM_ERR_TIMEOUT, after which the members' states are undefined
+ *    (lbm_reset them before going on).  General tiles stage serially on the
+ *    tile's node threads.  Results equal the graph schedule's to the FP32
+ *    parity tolerance (not bit for bit: the general tiles' staging is
+ *    compiled separately).
+ * The schedule applies from the next lbm_batch_step. */
+lbm_status lbm_batch_set_schedule(lbm_batch* b, int schedule);
+
+/* CTAs of the batch's last persistent launch (0 before the first). */
+lbm_status lbm_batch_persistent_grid(lbm_batch* b, int* ctas);
+
+/* Failure-detection test hook (host-side injection; no device fault).  From
+ * the next persistent launch on, every grid barrier waits for extra_arrivals
+ * more CTAs than the grid has, so a barrier with extra_arrivals > 0 can never
+ * complete and its waits run out after spin_limit_cycles SM clock cycles
+ * (<= 0: the default budget); the launch then ends and lbm_batch_sync
+ * reports LBM_ERR_TIMEOUT.  extra_arrivals = 0 restores normal operation.
+ * Waits for the batch stream first. */
+lbm_status lbm_batch_inject_barrier_fault(lbm_batch* b, int extra_arrivals, int64_t spin_limit_cycles);
 
 /* Release the batch (not its members).  NULL is ignored. */
 void lbm_batch_destroy(lbm_batch* b);

@@ -102,6 +102,9 @@ struct lbm_ctx {
     void* stage = nullptr;             // pinned staging buffer for host transfers
     size_t stage_bytes = 0;
     int timing_every = 0;
+    // persistent schedule of a single context: a batch of one member
+    int schedule = LBM_SCHEDULE_GRAPHS;
+    lbm_batch* solo = nullptr;
     std::vector<cudaEvent_t> ev_start, ev_mid, ev_stop;
     int n_samples = 0;
     std::string err;
@@ -126,10 +129,15 @@ lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
     } while (0)
 
 constexpr int kGraphSteps = 32;  // even: a replay leaves the ping-pong parity unchanged
+constexpr int kPersistSteps = 1024;  // steps per persistent launch
+// clock64 budget of one grid-barrier wait: ~1 s at the 2.07 GHz SM clock,
+// several hundred times the longest step of any batch measured
+constexpr long long kDefaultSpinLimit = 2000000000LL;
 constexpr int kMaxSamples = 4096;
 
 void free_ctx(lbm_ctx* c) {
     if (!c) return;
+    if (c->solo) lbm_batch_destroy(c->solo);
     for (int p = 0; p < 2; ++p)
         if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -833,6 +841,14 @@ struct lbm_batch {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int64_t launches = 0;
+    // persistent schedule: one cooperative launch per run of up to
+    // kPersistSteps steps, grid barriers with bounded waits between steps
+    int schedule = LBM_SCHEDULE_GRAPHS;
+    unsigned* pbar = nullptr;     // barrier arrivals (zeroed before each launch)
+    unsigned* pstatus = nullptr;  // PERSIST_TIMEOUT once a barrier wait ran out
+    long long spin_limit = kDefaultSpinLimit;
+    int bar_skew = 0;             // fault injection for tests: extra arrivals every barrier waits for
+    int persist_grid = 0;         // CTAs of the last persistent launch
     std::string err;
 };
 
@@ -964,13 +980,56 @@ cudaError_t batch_launch(lbm_batch* b, bool macros, cudaStream_t st, cudaStream_
     return e;
 }
 
-void batch_advance(lbm_batch* b, int64_t n) {
+void batch_advance(lbm_batch* b, int64_t n, int64_t launches = -1) {
     for (lbm_ctx* c : b->m) {
         if (n & 1) c->cur = 1 - c->cur;
         c->step += n;
     }
     if (n & 1) b->bpar ^= 1;
-    b->launches += n * ((b->nfast > 0) + (b->ngeneral > 0));
+    b->launches += launches >= 0 ? launches : n * ((b->nfast > 0) + (b->ngeneral > 0));
+}
+
+// n steps of every member as persistent launches (FP32 storage only).
+template <typename S, typename R>
+lbm_status batch_run_persistent(lbm_batch* b, int64_t n) {
+    if constexpr (!std::is_same<S, float>::value || !std::is_same<R, float>::value) {
+        (void)n;
+        return bfail(b, LBM_ERR_UNSUPPORTED, "the persistent schedule is built for FP32 storage only");
+    } else {
+        if (!b->pbar) {
+            BCK(cudaMalloc((void**)&b->pbar, sizeof(unsigned)));
+            BCK(cudaMalloc((void**)&b->pstatus, sizeof(unsigned)));
+            BCK(cudaMemsetAsync(b->pstatus, 0, sizeof(unsigned), b->stream));
+        }
+        const D2Args<S, R>* const* av = reinterpret_cast<const D2Args<S, R>* const*>(b->args);
+        int64_t rem = n;
+        while (rem > 0) {
+            const int chunk = (int)std::min<int64_t>(rem, kPersistSteps);
+            const bool last = chunk == rem;  // the call's last step writes the macroscopic fields
+            PersistArgs<S, R> p{};
+            p.args[0] = av[b->bpar];
+            p.args[1] = av[b->bpar ^ 1];
+            p.args_last[0] = last ? av[b->bpar + 2] : p.args[0];
+            p.args_last[1] = last ? av[(b->bpar ^ 1) + 2] : p.args[1];
+            p.blocks = b->blocks;
+            p.flags = b->flags;
+            p.slot = b->slot;
+            p.strips = b->strips;
+            p.member = b->member;
+            p.ntiles = b->nfast + b->ngeneral;
+            p.nfast = b->nfast;
+            p.nsteps = chunk;
+            p.bar = b->pbar;
+            p.pstatus = b->pstatus;
+            p.spin_limit = b->spin_limit;
+            p.bar_skew = b->bar_skew;
+            BCK(cudaMemsetAsync(b->pbar, 0, sizeof(unsigned), b->stream));
+            BCK((launch_d2q9_persist<S, R>(p, b->variant, b->stream, &b->persist_grid)));
+            batch_advance(b, chunk, 1);
+            rem -= chunk;
+        }
+        return LBM_OK;
+    }
 }
 
 template <typename S, typename R>
@@ -1012,6 +1071,7 @@ lbm_status batch_run(lbm_batch* b, int64_t n) {
             if (st != LBM_OK) return st;
             break;
         }
+    if (b->schedule == LBM_SCHEDULE_PERSISTENT) return batch_run_persistent<S, R>(b, n);
     int64_t rem = n;
     while (rem > 1) {
         if (b->use_graphs && rem - 1 >= kGraphSteps) {
@@ -1378,6 +1438,22 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
     if (c->d3) return lbm3::step(c->d3, nsteps);
     if (nsteps < 0) return fail(c, LBM_ERR_INVALID_ARG, "nsteps must be >= 0");
     if (nsteps == 0) return LBM_OK;
+    if (c->schedule == LBM_SCHEDULE_PERSISTENT) {
+        if (!c->solo) {
+            lbm_ctx* one[1] = {c};
+            lbm_status st = lbm_batch_create(one, 1, c->stream, &c->solo);
+            if (st == LBM_OK) st = lbm_batch_set_schedule(c->solo, LBM_SCHEDULE_PERSISTENT);
+            if (st != LBM_OK) {
+                const std::string msg = c->solo ? c->solo->err : lbm_last_error(nullptr);
+                lbm_batch_destroy(c->solo);
+                c->solo = nullptr;
+                return fail(c, st, msg);
+            }
+        }
+        lbm_status st = batch_run_any(c->solo, nsteps);
+        if (st != LBM_OK) return fail(c, st, c->solo->err);
+        return LBM_OK;
+    }
     if (c->precision == LBM_FP64) return run_steps<double, double>(c, nsteps);
     if (c->precision == LBM_FP32) return run_steps<float, float>(c, nsteps);
     return run_steps<__half, float>(c, nsteps);
@@ -1395,7 +1471,23 @@ lbm_status lbm_reset(lbm_ctx* c, const double* rho_init, const double* u_init) {
 lbm_status lbm_sync(lbm_ctx* c) {
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
     if (c->d3) return lbm3::sync(c->d3);
+    if (c->solo) {
+        lbm_status st = lbm_batch_sync(c->solo);
+        if (st != LBM_OK) return fail(c, st, c->solo->err);
+    }
     return check_status(c);
+}
+
+lbm_status lbm_set_schedule(lbm_ctx* c, int schedule) {
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
+    if (schedule != LBM_SCHEDULE_GRAPHS && schedule != LBM_SCHEDULE_PERSISTENT)
+        return fail(c, LBM_ERR_INVALID_ARG, "unknown schedule");
+    if (schedule == LBM_SCHEDULE_PERSISTENT && c->precision != LBM_FP32)
+        return fail(c, LBM_ERR_UNSUPPORTED, "the persistent schedule is built for FP32 storage only");
+    CK(cudaStreamSynchronize(c->stream));
+    c->schedule = schedule;
+    return LBM_OK;
 }
 
 lbm_status lbm_get_macros(lbm_ctx* c, float* rho, float* u, int dst_is_device) {
@@ -1674,6 +1766,15 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
 lbm_status lbm_batch_sync(lbm_batch* b) {
     if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "batch is NULL");
     BCK(cudaStreamSynchronize(b->stream));
+    if (b->pstatus) {
+        unsigned ps = 0;
+        BCK(cudaMemcpy(&ps, b->pstatus, sizeof(ps), cudaMemcpyDeviceToHost));
+        if (ps & PERSIST_TIMEOUT) {
+            BCK(cudaMemset(b->pstatus, 0, sizeof(unsigned)));  // reported once; reset the members to go on
+            return bfail(b, LBM_ERR_TIMEOUT,
+                         "a grid barrier of the persistent schedule timed out; the members' states are undefined");
+        }
+    }
     for (lbm_ctx* c : b->m) {
         lbm_status st = check_status(c);
         if (st != LBM_OK) return bfail(b, st, c->err);
@@ -1728,10 +1829,37 @@ lbm_status lbm_batch_set_graph_mode(lbm_batch* b, int use_graphs) {
     return LBM_OK;
 }
 
+lbm_status lbm_batch_set_schedule(lbm_batch* b, int schedule) {
+    if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "batch is NULL");
+    if (schedule != LBM_SCHEDULE_GRAPHS && schedule != LBM_SCHEDULE_PERSISTENT)
+        return bfail(b, LBM_ERR_INVALID_ARG, "unknown schedule");
+    if (schedule == LBM_SCHEDULE_PERSISTENT && b->precision != LBM_FP32)
+        return bfail(b, LBM_ERR_UNSUPPORTED, "the persistent schedule is built for FP32 storage only");
+    b->schedule = schedule;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_persistent_grid(lbm_batch* b, int* ctas) {
+    if (!b || !ctas) return bfail(b, LBM_ERR_INVALID_ARG, "NULL argument");
+    *ctas = b->persist_grid;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_inject_barrier_fault(lbm_batch* b, int extra_arrivals, int64_t spin_limit_cycles) {
+    if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "batch is NULL");
+    if (extra_arrivals < 0) return bfail(b, LBM_ERR_INVALID_ARG, "extra_arrivals must be >= 0");
+    BCK(cudaStreamSynchronize(b->stream));
+    b->bar_skew = extra_arrivals;
+    b->spin_limit = spin_limit_cycles > 0 ? (long long)spin_limit_cycles : kDefaultSpinLimit;
+    return LBM_OK;
+}
+
 void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     cudaStreamSynchronize(b->stream);
     free_batch_lists(b);
+    if (b->pbar) cudaFree(b->pbar);
+    if (b->pstatus) cudaFree(b->pstatus);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->side_stream) cudaStreamDestroy(b->side_stream);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);

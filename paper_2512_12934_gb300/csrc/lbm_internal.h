@@ -103,6 +103,36 @@ struct BatchArgs {
 template <typename S, typename R>
 cudaError_t launch_d2q9_batch(const BatchArgs<S, R>& b, int variant, bool general, int nblocks, cudaStream_t st);
 
+// Persistent multi-step launch over a batch's tile list (lbm_d2q9_persist.cu).
+// Step s of the launch uses the argument blocks args[s & 1] (args_last[s & 1]
+// for its last step, which writes the macroscopic fields); between steps the
+// grid waits at a barrier whose every wait is bounded by spin_limit clock64
+// cycles.  bar must be zero at launch; pstatus gets PERSIST_TIMEOUT when a
+// wait runs out.  bar_skew is added to every barrier target: 0 in normal
+// runs, > 0 only to test the timeout path (the barrier can then never
+// complete).
+constexpr unsigned PERSIST_TIMEOUT = 1u;
+
+template <typename S, typename R>
+struct PersistArgs {
+    const D2Args<S, R>* args[2];
+    const D2Args<S, R>* args_last[2];
+    const int* blocks;
+    const uint8_t* flags;
+    const int* slot;
+    const unsigned* strips;
+    const int* member;
+    int ntiles, nfast, nsteps;
+    unsigned* bar;
+    unsigned* pstatus;
+    long long spin_limit;
+    int bar_skew;
+};
+
+// grid_out (may be NULL): the number of CTAs launched.
+template <typename S, typename R>
+cudaError_t launch_d2q9_persist(const PersistArgs<S, R>& p, int variant, cudaStream_t st, int* grid_out);
+
 // Launch one list of tiles of one step: general = false -> fast kernel,
 // true -> general kernel; nblocks list entries starting at a.list_off.
 template <typename S, typename R>

@@ -107,29 +107,44 @@ extern "C" lbm_status lbm_mass_noalloc(const void* f, int precision, int nx, int
                       kNoAllocMaxRows);
         return reject(LBM_ERR_INVALID_ARG, msg);
     }
+    // An error left pending by earlier, unrelated work on this thread is not
+    // ours to report or to clear: refuse before launching anything.
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return reject(LBM_ERR_CUDA, "lbm_mass_noalloc: a CUDA error from earlier work is pending");
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return reject(LBM_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return reject(LBM_ERR_UNSUPPORTED, "lbm_mass_noalloc: device index too large");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return reject(LBM_ERR_CUDA, cudaGetErrorString(e));
     double* rows;
     {
-        // First call on this device (with it current): resolve the device
-        // address of the scratch array.  The host-side symbol is only a
-        // stand-in and must never reach a kernel.
+        // The device address of the scratch array: the host-side symbol is
+        // only a stand-in and must never reach a kernel.  Outside a stream
+        // capture it is resolved on every call in the current context (a
+        // cached address would be stale after cudaDeviceReset, or belong to
+        // another context); inside a capture the address resolved by the
+        // last call on this device outside a capture is used.
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_row_partials);
             if (e != cudaSuccess) return reject(LBM_ERR_CUDA, cudaGetErrorString(e));
             g_scratch_ptr[dev] = static_cast<double*>(p);
+        } else if (!g_scratch_ptr[dev]) {
+            return reject(LBM_ERR_INVALID_ARG,
+                          "lbm_mass_noalloc: the first call on a device must come before any stream capture");
         }
         rows = g_scratch_ptr[dev];
     }
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == LBM_FP32)
         mass_rows_kernel<float><<<ny, 256, 0, st>>>(static_cast<const float*>(f), nx, ny, pitch, solid, rows);
     else
         mass_rows_kernel<double><<<ny, 256, 0, st>>>(static_cast<const double*>(f), nx, ny, pitch, solid, rows);
+    e = cudaGetLastError();  // nothing was pending, so a launch error here is this call's
+    if (e != cudaSuccess) return reject(LBM_ERR_CUDA, cudaGetErrorString(e));
     mass_finish_kernel<<<1, 256, 0, st>>>(rows, ny, mass);
     e = cudaGetLastError();
     if (e != cudaSuccess) return reject(LBM_ERR_CUDA, cudaGetErrorString(e));

@@ -19,6 +19,7 @@ LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_FP32, LBM_FP32_FP16STORE, LBM_FP64 = 0, 1, 2
 PRECISIONS = {"fp32": LBM_FP32, "fp16store": LBM_FP32_FP16STORE, "fp64": LBM_FP64}
 LBM_INLET_VELOCITY, LBM_OUTLET_CONVECTIVE = 1, 2
+SCHEDULES = {"graphs": 0, "persistent": 1}
 SIDES = {"xmin": 0, "xmax": 1, "ymin": 2, "ymax": 3, "zmin": 4, "zmax": 5}
 
 
@@ -112,11 +113,19 @@ def load():
     L.lbm_tile_stats.argtypes = [c_ctx] + [ctypes.POINTER(ctypes.c_int)] * 3 + [ctypes.POINTER(ctypes.c_int64)] * 2
     L.lbm_set_graph_mode.restype = ctypes.c_int
     L.lbm_set_graph_mode.argtypes = [c_ctx, ctypes.c_int]
+    L.lbm_set_schedule.restype = ctypes.c_int
+    L.lbm_set_schedule.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_mass_noalloc.restype = ctypes.c_int
     L.lbm_mass_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.lbm_batch_create.restype = ctypes.c_int
     L.lbm_batch_create.argtypes = [ctypes.POINTER(c_ctx), ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(c_ctx)]
+    L.lbm_batch_set_schedule.restype = ctypes.c_int
+    L.lbm_batch_set_schedule.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.lbm_batch_persistent_grid.restype = ctypes.c_int
+    L.lbm_batch_persistent_grid.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+    L.lbm_batch_inject_barrier_fault.restype = ctypes.c_int
+    L.lbm_batch_inject_barrier_fault.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]
     L.lbm_batch_step.restype = ctypes.c_int
     L.lbm_batch_step.argtypes = [c_ctx, ctypes.c_int64]
     L.lbm_batch_sync.restype = ctypes.c_int
@@ -335,6 +344,10 @@ class Solver:
     def set_graph_mode(self, on):
         _check(load().lbm_set_graph_mode(self.h, int(bool(on))), self.h)
 
+    def set_schedule(self, name):
+        """'graphs' (default) or 'persistent' (lbm_set_schedule)."""
+        _check(load().lbm_set_schedule(self.h, SCHEDULES[name]), self.h)
+
     def autotune(self, steps=20):
         v = ctypes.c_int()
         ms = ctypes.c_double()
@@ -391,6 +404,20 @@ class Batch:
 
     def set_graph_mode(self, on):
         self._check(load().lbm_batch_set_graph_mode(self.h, int(bool(on))))
+
+    def set_schedule(self, name):
+        """'graphs' (default) or 'persistent' (lbm_batch_set_schedule)."""
+        self._check(load().lbm_batch_set_schedule(self.h, SCHEDULES[name]))
+
+    def persistent_grid(self):
+        n = ctypes.c_int()
+        self._check(load().lbm_batch_persistent_grid(self.h, ctypes.byref(n)))
+        return n.value
+
+    def inject_barrier_fault(self, extra_arrivals, spin_limit_cycles=0):
+        """Test hook: persistent barriers wait for `extra_arrivals` CTAs that
+        never come, so their bounded waits run out (LBM_ERR_TIMEOUT)."""
+        self._check(load().lbm_batch_inject_barrier_fault(self.h, int(extra_arrivals), int(spin_limit_cycles)))
 
     def close(self):
         if getattr(self, "h", None):
