@@ -156,20 +156,27 @@ lbm_status lbm_create(const lbm_grid* grid, const lbm_params* params,
  * state is cleared (lambda = 0, chi = 1), the step counter returns to 0. */
 lbm_status lbm_reset(lbm_ctx* ctx, const double* rho_init, const double* u_init);
 
-/* Enqueue nsteps time steps (nsteps >= 0) on the context's stream.  Each
- * step is one fused launch: pull streaming (Eq. 2) with halfway bounce-back
- * (Eq. B1) and periodic wrap (Eq. B2); inlet reconstruction (Eqs. 13-19);
- * convective outlet (Eqs. 20, 21); densities and pseudopotentials with
- * ghost mirrors (Eqs. 24, 25); forces (Eqs. 10, 11); common velocity
- * (Eqs. 7, 8) with the outlet rescaled by chi (Eq. 22); MRT collision with
- * forcing (Eqs. 1, 3-6, 9); and the FP64 flux reductions that give lambda
- * and chi for the next step (Eqs. 21, 23).  Returns without waiting for the
- * GPU; launch errors are reported at once, divergence by the next call
- * that synchronises (lbm_sync, lbm_get_*). */
+/* Enqueue nsteps time steps (nsteps >= 0) on the context's stream.  A step
+ * performs, fused per tile of nodes: pull streaming (Eq. 2) with halfway
+ * bounce-back (Eq. B1) and periodic wrap (Eq. B2); inlet reconstruction
+ * (Eqs. 13-19); convective outlet (Eqs. 20, 21); densities and
+ * pseudopotentials with ghost mirrors (Eqs. 24, 25); forces (Eqs. 10, 11);
+ * common velocity (Eqs. 7, 8) with the outlet rescaled by chi (Eq. 22); MRT
+ * collision with forcing (Eqs. 1, 3-6, 9); and the FP64 flux reductions that
+ * give lambda and chi for the next step (Eqs. 21, 23).  D2Q9 launches per
+ * step (graph schedule): one for the general tiles (those that see an open
+ * face) and one for the other tiles, plus one for the column-marching runs
+ * under tile variant 4 (FP32); the persistent schedule runs up to 1024
+ * steps per launch.  D3Q19: five launches per step (pulls, face pulls,
+ * collision, outlet, reduction).  Returns without waiting for the GPU;
+ * launch errors are reported at once, divergence (LBM_ERR_DIVERGED) or a
+ * bounded device wait that ran out (LBM_ERR_TIMEOUT) by the next call that
+ * synchronises (lbm_sync, lbm_get_*). */
 lbm_status lbm_step(lbm_ctx* ctx, int64_t nsteps);
 
 /* Wait for the context's stream; LBM_ERR_DIVERGED if a non-finite density
- * or velocity was produced since creation. */
+ * or velocity was produced since creation (or the last lbm_reset),
+ * LBM_ERR_TIMEOUT if a bounded device wait ran out. */
 lbm_status lbm_sync(lbm_ctx* ctx);
 
 /* Macroscopic fields used by the most recent collision (after creation:
@@ -215,7 +222,14 @@ lbm_status lbm_kernel_time_split(lbm_ctx* ctx, double* fast_ms, double* general_
  * 0: 32x8, 1: 32x4, 2: 64x4, 3: 32x16 nodes per CTA (default: 1 below 2^22
  * nodes, else 0).  Bit-identical results on grids without open faces; with
  * open faces the FP64 flux partials are grouped per tile, so chi may differ
- * in its last bit. */
+ * in its last bit.  Variant 4 tiles like variant 0 and, for FP32 storage,
+ * runs the interior tiles (those whose pulls and interaction stencil stay
+ * inside the grid and away from open faces) through the column-marching
+ * kernel: one CTA per run of up to 64 tiles of a tile column, one TMA bulk
+ * copy of all 18 population planes per 8 rows, pulls from shared memory.
+ * Same method; results agree with variant 0 to FP32 rounding.  Other
+ * precisions run variant 4 exactly as variant 0.  Batches and the
+ * persistent schedule run variant 4 members as variant 0. */
 lbm_status lbm_set_tile_variant(lbm_ctx* ctx, int variant);
 int lbm_num_tile_variants(void);
 
@@ -283,7 +297,8 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int n, void* cuda_stream, l
  * CUDA graphs); members' macroscopic fields are written by the last one. */
 lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
 
-/* Wait for the batch stream; LBM_ERR_DIVERGED if any member diverged. */
+/* Wait for the batch stream; LBM_ERR_DIVERGED if any member diverged,
+ * LBM_ERR_TIMEOUT if a persistent launch's barrier wait ran out. */
 lbm_status lbm_batch_sync(lbm_batch* b);
 
 /* Re-tile every member with `variant` (see lbm_set_tile_variant). */
@@ -294,7 +309,8 @@ lbm_status lbm_batch_set_tile_variant(lbm_batch* b, int variant);
  * fastest.  variant: the choice; ms_per_step (may be NULL): its time. */
 lbm_status lbm_batch_autotune(lbm_batch* b, int steps, int* variant, double* ms_per_step);
 
-/* The same for a single context. */
+/* The same for a single context (tile variants 0-3; FP32 contexts also time
+ * the column-marching variant 4 on the context itself). */
 lbm_status lbm_autotune(lbm_ctx* ctx, int steps, int* variant, double* ms_per_step);
 
 /* Tile variant, number of tiles in the batch's fast and general lists and

@@ -205,6 +205,7 @@ typedef struct {
     double body[2];   /* body-force density, shared by rho_k / rho */
     int use_s_full;   /* 1: S taken verbatim from s_full (textbook reductions) */
     double s_full[2][NQ];
+    int chi_same_step; /* 1: chi of Eq. 23 from this step's fields (t + dt, as printed); 0: lagged */
 } orc_params;
 
 typedef struct {
@@ -436,6 +437,43 @@ void orc_set_threads(orc_state* st, int threads) {
     st->threads = threads > 0 ? threads : 1;
 }
 
+/* Mass fluxes of Eqs. 21 and 23 over the current fields: Q_in at the inlet
+ * nodes x1, Q_out and the normal-speed sum at the outlet's inward neighbours
+ * x_{N-1} (count in *m).  Returns 1 if the domain has an outlet. */
+static int face_fluxes(const orc_state* st, double* qin, double* qout, double* usum, int* m, int* have_in) {
+    const int nx = st->nx, N = st->N;
+    const double* rho = st->rho;
+    const double* u = st->u;
+    int have_out = 0;
+    *qin = *qout = *usum = 0.0;
+    *m = 0;
+    *have_in = 0;
+    for (int fi = 0; fi < st->nfaces; ++fi) {
+        const orc_face* fc = &st->face[fi];
+        int ox, oy;
+        side_normal(fc->side, &ox, &oy);
+        for (int t = fc->lo; t <= fc->hi; ++t) {
+            int x, y;
+            face_node(st, fc, t, &x, &y);
+            int n1 = y * nx + x;
+            if (st->solid[n1]) continue;
+            if (fc->kind == 1) {
+                *have_in = 1;
+                double un = -(ox * u[n1] + oy * u[N + n1]);
+                *qin += (rho[n1] + rho[N + n1]) * un;
+            } else {
+                have_out = 1;
+                int n2 = (y - oy) * nx + (x - ox);
+                double un = ox * u[n2] + oy * u[N + n2];
+                *qout += (rho[n2] + rho[N + n2]) * un;
+                *usum += un;
+                *m += 1;
+            }
+        }
+    }
+    return have_out;
+}
+
 /* One full time step in the canonical order:
  * stream + bounce-back + periodic -> inlet (Eq. 13, alpha) -> outlet (Eq. 20)
  * -> rho, psi, ghosts -> forces -> u^eq (chi at the outlet) -> collision
@@ -618,6 +656,16 @@ static void one_step(orc_state* st) {
             u[N + n] = jy / rt;
         }
 
+    /* Eq. 23 as printed (t + dt): chi from this step's velocities, before
+     * Eq. 22 uses it (lambda stays lagged: Eq. 20 needs it before the
+     * velocities of this step exist) */
+    if (st->p.chi_same_step) {
+        double qi, qo, us;
+        int mm, hin;
+        if (face_fluxes(st, &qi, &qo, &us, &mm, &hin) && mm > 0)
+            st->chi = (!hin || fabs(qo) < 1e-14) ? 1.0 : qi / qo;
+    }
+
     /* Eq. 22: outlet normal velocity = chi * that of the node x_{N-1} */
     for (int fi = 0; fi < st->nfaces; ++fi) {
         const orc_face* fc = &st->face[fi];
@@ -654,31 +702,9 @@ static void one_step(orc_state* st) {
     }
 
     /* 8. reductions that set lambda (Eq. 21) and chi (Eq. 23) for the next step */
-    double qin = 0.0, qout = 0.0, usum = 0.0;
-    int have_in = 0, have_out = 0, mcount = 0;
-    for (int fi = 0; fi < st->nfaces; ++fi) {
-        const orc_face* fc = &st->face[fi];
-        int ox, oy;
-        side_normal(fc->side, &ox, &oy);
-        for (int t = fc->lo; t <= fc->hi; ++t) {
-            int x, y;
-            face_node(st, fc, t, &x, &y);
-            int n1 = y * nx + x;
-            if (st->solid[n1]) continue;
-            if (fc->kind == 1) {
-                have_in = 1;
-                double un = -(ox * u[n1] + oy * u[N + n1]);
-                qin += (rho[n1] + rho[N + n1]) * un;
-            } else {
-                have_out = 1;
-                int n2 = (y - oy) * nx + (x - ox);
-                double un = ox * u[n2] + oy * u[N + n2];
-                qout += (rho[n2] + rho[N + n2]) * un;
-                usum += un;
-                ++mcount;
-            }
-        }
-    }
+    double qin, qout, usum;
+    int have_in, mcount;
+    int have_out = face_fluxes(st, &qin, &qout, &usum, &mcount, &have_in);
     st->Qin = qin;
     st->Qout = qout;
     if (have_out && mcount > 0) {

@@ -38,7 +38,11 @@ Readings taken where the paper is silent, garbled or inconsistent:
     previous step (one-step lag); lambda is the mean of u^eq.n over the
     fluid nodes of column x_{N-1}, clamped at >= 0; chi = Q_in / Q_out with
     Q over (rho_1 + rho_2) u^eq.n; chi = 1 when |Q_out| < 1e-14 or there
-    is no inlet.  lambda = 0 and chi = 1 before the first step.
+    is no inlet.  lambda = 0 and chi = 1 before the first step.  With
+    cfg["chi_same_step"] = 1, chi is taken from the step's own velocities
+    (t + dt, as Eq. 23 prints it) just before Eq. 22 uses it; lambda cannot
+    be (Eq. 20 needs it before the step's velocities exist) and stays
+    lagged.
 10. Eq. 22 overwrites the outlet node's normal component of u^eq (the
     velocity the collision uses) with chi times that of x_{N-1}, same row;
     the tangential component is kept.
@@ -66,7 +70,7 @@ class _Params(ctypes.Structure):
         ("G12", ctypes.c_double), ("Gw", ctypes.c_double * 2), ("nu", ctypes.c_double * 2),
         ("s_e", ctypes.c_double), ("s_q", ctypes.c_double), ("s_eps_mode", ctypes.c_int),
         ("body", ctypes.c_double * 2), ("use_s_full", ctypes.c_int),
-        ("s_full", (ctypes.c_double * 9) * 2),
+        ("s_full", (ctypes.c_double * 9) * 2), ("chi_same_step", ctypes.c_int),
     ]
 
 
@@ -189,6 +193,7 @@ class Oracle2D:
         p.s_eps_mode = int(cfg.get("s_eps_mode", 1))
         body = cfg.get("body", (0.0, 0.0))
         p.body[0], p.body[1] = body[0], body[1]
+        p.chi_same_step = int(cfg.get("chi_same_step", 0))
         sf = cfg.get("s_full")
         if sf is not None:
             p.use_s_full = 1

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_d2q9.cu", "lbm_d2q9_persist.cu", "lbm_noalloc.cu", "lbm_mlp.cu", "lbm_d3q19.cu", "lbm_d3q19_host.cu"]
+SOURCES = ["lbm_api.cu", "lbm_d2q9.cu", "lbm_d2q9_persist.cu", "lbm_d2q9_march.cu", "lbm_noalloc.cu", "lbm_mlp.cu", "lbm_d3q19.cu", "lbm_d3q19_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

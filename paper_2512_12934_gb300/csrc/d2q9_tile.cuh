@@ -1347,9 +1347,14 @@ __host__ __device__ constexpr int gen_threads() {
     return ROLES ? GenRoles<TX, TY>::THREADS : TX * TY;
 }
 
+// The warps of a CTA are spread over the SM's four sub-partitions, each with
+// 16 K registers, so the cap must let ceil(warps / 4) warps fit in 16 K (a
+// cap checked against the whole 64 K file alone can leave a block that does
+// not launch: 17 warps at 120 registers need 19,200 in one sub-partition).
 template <typename R, int TX, int TY, bool ROLES>
 __host__ __device__ constexpr int gen_maxreg() {
-    constexpr int fit = 65536 / gen_threads<TX, TY, ROLES>() / 8 * 8;
+    constexpr int warps = (gen_threads<TX, TY, ROLES>() + 31) / 32;
+    constexpr int fit = 16384 / (((warps + 3) / 4) * 32) / 8 * 8;
     constexpr int want = sizeof(R) == 4 ? 80 : 128;
     return want < fit ? want : fit;
 }

@@ -2,6 +2,7 @@
 // per-node descriptors, device allocation, the step loop over the fused
 // kernel, FP64 diagnostics and checkpoints.
 #include <cuda_fp16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,6 +65,12 @@ struct lbm_ctx {
     unsigned* block_strips = nullptr;
     int nfast = 0, ngeneral = 0;
     int64_t fast_nodes = 0, general_nodes = 0;  // fluid nodes owned by each tile list
+    // column-marching variant: runs of interior tiles, one CTA each
+    int4* march_runs = nullptr;
+    uint8_t* march_flags = nullptr;
+    int nmarch = 0, march_tiles = 0;
+    CUtensorMap tmap[2];  // TMA descriptors of f[0], f[1] as [18][ny][pitch] floats
+    int have_tmap = 0;
     int64_t tiling_gen = 0;                      // bumped whenever the tile lists are rebuilt
     void* uin = nullptr;
     void* Fp[2] = {nullptr, nullptr};
@@ -147,7 +154,7 @@ void free_ctx(lbm_ctx* c) {
     for (cudaEvent_t e : c->ev_start) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_mid) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
-    void* ptrs[] = {c->f[0], c->f[1], c->info, c->blocks, c->block_flags, c->block_strips, c->uin, c->Fp[0], c->Fp[1], c->fo[0], c->fo[1],
+    void* ptrs[] = {c->march_runs, c->march_flags, c->f[0], c->f[1], c->info, c->blocks, c->block_flags, c->block_strips, c->uin, c->Fp[0], c->Fp[1], c->fo[0], c->fo[1],
                     c->scal[0], c->scal[1], c->partials[0], c->partials[1], c->block_slot, c->status,
                     c->macro, c->diag_partials, c->rref[0], c->rref[1]};
     for (void* p : ptrs)
@@ -228,6 +235,10 @@ cudaError_t launch_lists(lbm_ctx* c, bool macros, cudaStream_t st, cudaStream_t 
     D2Args<S, R> ag = a;
     ag.list_off = c->nfast;
     if (fork && e == cudaSuccess) e = launch_d2q9_step<S, R>(ag, c->variant, true, c->ngeneral, side);
+    if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
+        if (e == cudaSuccess && c->nmarch > 0)
+            e = launch_d2q9_march(a, &c->tmap[c->cur], c->march_runs, c->march_flags, c->nmarch, st);
+    }
     if (e == cudaSuccess) e = launch_d2q9_step<S, R>(a, c->variant, false, c->nfast, st);
     if (e == cudaSuccess && mid) e = cudaEventRecord(mid, st);
     if (!fork && e == cudaSuccess) e = launch_d2q9_step<S, R>(ag, c->variant, true, c->ngeneral, st);
@@ -245,7 +256,7 @@ lbm_status launch_one(lbm_ctx* c, bool macros, cudaStream_t st, cudaEvent_t mid 
     // the ping-pong slot written by this step becomes current
     c->cur = 1 - c->cur;
     c->step += 1;
-    c->launches += (c->nfast > 0) + (c->ngeneral > 0);
+    c->launches += (c->nfast > 0) + (c->ngeneral > 0) + (c->nmarch > 0);
     return LBM_OK;
 }
 
@@ -290,7 +301,7 @@ lbm_status run_plain(lbm_ctx* c, int64_t cnt) {
         cudaError_t e = cudaGraphLaunch(c->gexec[c->cur], c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "step graph launch");
         c->step += kGraphSteps;
-        c->launches += (int64_t)kGraphSteps * ((c->nfast > 0) + (c->ngeneral > 0));
+        c->launches += (int64_t)kGraphSteps * ((c->nfast > 0) + (c->ngeneral > 0) + (c->nmarch > 0));
         cnt -= kGraphSteps;
     }
     for (; cnt > 0; --cnt) {
@@ -462,6 +473,8 @@ lbm_status check_status(lbm_ctx* c) {
     unsigned int st = 0;
     CK(cudaMemcpyAsync(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (st & 4u) return fail(c, LBM_ERR_CUDA, "a bulk-copy destination was not 128-byte aligned; nothing was copied");
+    if (st & 2u) return fail(c, LBM_ERR_TIMEOUT, "a bounded wait for a bulk copy ran out");
     if (st) return fail(c, LBM_ERR_DIVERGED, "non-finite density or velocity produced");
     return LBM_OK;
 }
@@ -581,6 +594,37 @@ lbm_status fold_partials(lbm_ctx* c) {
 }
 
 // (Re)build the tile grid and the two tile lists for tile-shape variant v.
+// TMA descriptors of both population buffers for the column-marching
+// kernel: a float tensor [18][ny][pitch] with a box of 44 x 10 x 18
+// (columns x rows x planes).  cuTensorMapEncodeTiled comes from the driver
+// through the runtime's entry-point query, so no driver library is linked.
+lbm_status make_tensor_maps(lbm_ctx* c) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(c, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        encode = reinterpret_cast<Encode>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, 18};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * 4, (cuuint64_t)c->plane * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)D2Q9_MARCH_BOX_W, (cuuint32_t)D2Q9_MARCH_BOX_H, 18};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int p = 0; p < 2; ++p) {
+        CUresult r = encode(&c->tmap[p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->f[p], dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(c, LBM_ERR_CUDA, "cuTensorMapEncodeTiled rejected the population layout");
+    }
+    c->have_tmap = 1;
+    return LBM_OK;
+}
+
 lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
     if (v < 0 || v >= d2q9_num_variants()) return fail(c, LBM_ERR_INVALID_ARG, "unknown tile variant");
     if (sync_first) CK(cudaStreamSynchronize(c->stream));
@@ -713,6 +757,47 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
                 fl_fast.push_back(fl);
             }
         }
+    // column-marching variant: interior tiles (neither edge nor general)
+    // leave the fast list and form runs along their tile column
+    std::vector<int4> runs;
+    std::vector<uint8_t> run_fl;
+    if (v == D2Q9_MARCH_VARIANT && c->precision == LBM_FP32) {
+        std::vector<int> col_flag((size_t)c->gdim.x * c->gdim.y, -1);
+        std::vector<int> keep;
+        std::vector<uint8_t> keep_fl;
+        for (size_t t = 0; t < list_fast.size(); ++t) {
+            const int bx = list_fast[t] & 0xffff, by = list_fast[t] >> 16;
+            if (fl_fast[t] & BLOCK_EDGE) {
+                keep.push_back(list_fast[t]);
+                keep_fl.push_back(fl_fast[t]);
+            } else {
+                col_flag[(size_t)bx * c->gdim.y + by] = fl_fast[t];
+            }
+        }
+        int64_t interior = (int64_t)list_fast.size() - (int64_t)keep.size();
+        int sms = 152, dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // segment length: about eight runs per SM (two resident at a time), 2 to 64 tiles
+        const int seg = (int)std::min<int64_t>(64, std::max<int64_t>(2, (interior + 8 * sms - 1) / (8 * sms)));
+        for (unsigned bx = 0; bx < c->gdim.x; ++bx) {
+            unsigned by = 0;
+            while (by < c->gdim.y) {
+                if (col_flag[(size_t)bx * c->gdim.y + by] < 0) {
+                    ++by;
+                    continue;
+                }
+                unsigned end = by;
+                while (end < c->gdim.y && col_flag[(size_t)bx * c->gdim.y + end] >= 0 && (int)(end - by) < seg) ++end;
+                runs.push_back(make_int4((int)bx | ((int)by << 16), (int)(end - by), (int)run_fl.size(), 0));
+                for (unsigned t = by; t < end; ++t) run_fl.push_back((uint8_t)col_flag[(size_t)bx * c->gdim.y + t]);
+                by = end;
+            }
+        }
+        list_fast.swap(keep);
+        fl_fast.swap(keep_fl);
+    }
+    c->nmarch = (int)runs.size();
+    c->march_tiles = (int)run_fl.size();
     c->nfast = (int)list_fast.size();
     c->ngeneral = (int)list_gen.size();
     c->fast_nodes = fast_nodes_cnt;
@@ -726,7 +811,10 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
     std::vector<unsigned> strip_all((size_t)c->nfast, 0u);
     strip_all.insert(strip_all.end(), strips_gen.begin(), strips_gen.end());
 
-    void* old[] = {c->blocks, c->block_flags, c->block_slot, c->block_strips, c->partials[0], c->partials[1]};
+    void* old[] = {c->blocks, c->block_flags, c->block_slot, c->block_strips, c->partials[0], c->partials[1],
+                   c->march_runs, c->march_flags};
+    c->march_runs = nullptr;
+    c->march_flags = nullptr;
     for (void* p : old)
         if (p) cudaFree(p);
     c->blocks = nullptr;
@@ -751,6 +839,16 @@ lbm_status build_tiles(lbm_ctx* c, int v, bool sync_first) {
     CK(cudaMemcpy(c->blocks, blist.data(), blist.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->block_flags, bflags.data(), bflags.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->block_slot, slot_all.data(), slot_all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (c->nmarch > 0) {
+        CK(cudaMalloc((void**)&c->march_runs, runs.size() * sizeof(int4)));
+        CK(cudaMalloc((void**)&c->march_flags, run_fl.size()));
+        CK(cudaMemcpy(c->march_runs, runs.data(), runs.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->march_flags, run_fl.data(), run_fl.size(), cudaMemcpyHostToDevice));
+        if (!c->have_tmap) {
+            lbm_status ts = make_tensor_maps(c);
+            if (ts != LBM_OK) return ts;
+        }
+    }
     // a new tiling renumbers the slots: old partials are void (folded above)
     CK(cudaMemset(c->scal[0] + 5, 0, sizeof(double)));
     CK(cudaMemset(c->scal[1] + 5, 0, sizeof(double)));
@@ -889,7 +987,7 @@ template <typename S, typename R>
 lbm_status build_batch(lbm_batch* b) {
     // one kernel instantiation serves the whole batch: every member must use
     // the tile shape of the first one (members re-tiled on their own follow)
-    const int v = b->m[0]->variant;
+    const int v = d2q9_tile_kernel_variant(b->m[0]->variant);
     for (lbm_ctx* c : b->m)
         if (c->variant != v) {
             lbm_status st = build_tiles(c, v, true);
@@ -1126,7 +1224,7 @@ lbm_status batch_autotune(lbm_batch* b, int steps, int* chosen, double* best_ms)
     int best = -1;
     double bestms = 1e300;
     lbm_status st = LBM_OK;
-    for (int v = 0; v < d2q9_num_variants() && st == LBM_OK; ++v) {
+    for (int v = 0; v < D2Q9_MARCH_VARIANT && st == LBM_OK; ++v) {
         for (size_t i = 0; i < b->m.size() && st == LBM_OK; ++i) {
             st = restore_snapshot(b->m[i], &snaps[i]);
             if (st == LBM_OK) st = build_tiles(b->m[i], v, true);
@@ -1162,6 +1260,46 @@ lbm_status batch_autotune(lbm_batch* b, int steps, int* chosen, double* best_ms)
     *chosen = best;
     if (best_ms) *best_ms = bestms / steps;
     return st;
+}
+
+// Time `steps` steps of the column-marching variant on the context itself
+// from its current state (restored afterwards) and keep it if it beats
+// best_ms per step; otherwise the context keeps the tile variant *variant.
+lbm_status autotune_march(lbm_ctx* c, int steps, int* variant, double* best_ms) {
+    Snapshot snap;
+    lbm_status st = take_snapshot(c, &snap);
+    if (st != LBM_OK) return st;
+    const int best = *variant;
+    st = build_tiles(c, D2Q9_MARCH_VARIANT, true);
+    double ms = 1e300;
+    if (st == LBM_OK && c->nmarch > 0) {
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        CK(cudaEventCreate(&t0));
+        CK(cudaEventCreate(&t1));
+        st = run_steps<float, float>(c, std::max(2, steps / 4));  // warm-up (also captures the graphs)
+        if (st == LBM_OK) {
+            CK(cudaEventRecord(t0, c->stream));
+            st = run_steps<float, float>(c, steps);
+            CK(cudaEventRecord(t1, c->stream));
+            CK(cudaEventSynchronize(t1));
+            float el = 0.0f;
+            CK(cudaEventElapsedTime(&el, t0, t1));
+            ms = el / steps;
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+    }
+    lbm_status s2 = restore_snapshot(c, &snap);
+    const bool take = st == LBM_OK && ms < *best_ms;
+    if (s2 == LBM_OK) s2 = build_tiles(c, take ? D2Q9_MARCH_VARIANT : best, true);
+    free_snapshot(&snap);
+    if (st != LBM_OK) return st;
+    if (s2 != LBM_OK) return s2;
+    if (take) {
+        *variant = D2Q9_MARCH_VARIANT;
+        *best_ms = ms;
+    }
+    return LBM_OK;
 }
 
 }  // namespace
@@ -1708,7 +1846,7 @@ lbm_status lbm_tile_stats(lbm_ctx* c, int* variant, int* fast_tiles, int* genera
         return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
     if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
     *variant = c->variant;
-    *fast_tiles = c->nfast;
+    *fast_tiles = c->nfast + c->march_tiles;
     *general_tiles = c->ngeneral;
     *fast_nodes = c->fast_nodes;
     *general_nodes = c->general_nodes;
@@ -1807,9 +1945,12 @@ lbm_status lbm_autotune(lbm_ctx* c, int steps, int* variant, double* ms_per_step
     lbm_ctx* one[1] = {c};
     lbm_status st = lbm_batch_create(one, 1, c->stream, &b);
     if (st != LBM_OK) return fail(c, st, lbm_last_error(nullptr));
-    st = batch_autotune(b, steps, variant, ms_per_step);
+    double best_ms = 0.0;
+    st = batch_autotune(b, steps, variant, &best_ms);
     if (st != LBM_OK) fail(c, st, b->err);
     lbm_batch_destroy(b);
+    if (st == LBM_OK && c->precision == LBM_FP32) st = autotune_march(c, steps, variant, &best_ms);
+    if (st == LBM_OK && ms_per_step) *ms_per_step = best_ms;
     return st;
 }
 

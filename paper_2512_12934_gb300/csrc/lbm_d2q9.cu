@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) d2q9_diag_kernel(const S* __restrict__ f,
 }  // namespace
 
 struct TileShape { int tx, ty; };
-static const TileShape kVariants[] = {{32, 8}, {32, 4}, {64, 4}, {32, 16}};
+static const TileShape kVariants[] = {{32, 8}, {32, 4}, {64, 4}, {32, 16}, {32, 8}};
 
 void d2q9_variant_tile(int variant, int* tx, int* ty) {
     *tx = kVariants[variant].tx;
@@ -190,7 +190,7 @@ static void launch_batch_tile(const BatchArgs<S, R>& b, bool general, int nblock
 template <typename S, typename R>
 cudaError_t launch_d2q9_batch(const BatchArgs<S, R>& b, int variant, bool general, int nblocks, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
-    switch (variant) {
+    switch (d2q9_tile_kernel_variant(variant)) {
     case 0: launch_batch_tile<S, R, 32, 8>(b, general, nblocks, st); break;
     case 1: launch_batch_tile<S, R, 32, 4>(b, general, nblocks, st); break;
     case 2: launch_batch_tile<S, R, 64, 4>(b, general, nblocks, st); break;
@@ -203,7 +203,7 @@ cudaError_t launch_d2q9_batch(const BatchArgs<S, R>& b, int variant, bool genera
 template <typename S, typename R>
 cudaError_t launch_d2q9_step(const D2Args<S, R>& a, int variant, bool general, int nblocks, cudaStream_t st) {
     if (nblocks <= 0) return cudaSuccess;
-    switch (variant) {
+    switch (d2q9_tile_kernel_variant(variant)) {
     case 0: launch_tile<S, R, 32, 8>(a, general, nblocks, st); break;
     case 1: launch_tile<S, R, 32, 4>(a, general, nblocks, st); break;
     case 2: launch_tile<S, R, 64, 4>(a, general, nblocks, st); break;

@@ -107,7 +107,7 @@ cudaError_t persist_launch_tile(const PersistArgs<S, R>& p, cudaStream_t st, int
 template <typename S, typename R>
 cudaError_t launch_d2q9_persist(const PersistArgs<S, R>& p, int variant, cudaStream_t st, int* grid_out) {
     if (p.ntiles <= 0 || p.nsteps <= 0) return cudaSuccess;
-    switch (variant) {
+    switch (d2q9_tile_kernel_variant(variant)) {
     case 0: return persist_launch_tile<S, R, 32, 8>(p, st, grid_out);
     case 1: return persist_launch_tile<S, R, 32, 4>(p, st, grid_out);
     case 2: return persist_launch_tile<S, R, 64, 4>(p, st, grid_out);

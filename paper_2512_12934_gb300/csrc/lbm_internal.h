@@ -138,9 +138,23 @@ cudaError_t launch_d2q9_persist(const PersistArgs<S, R>& p, int variant, cudaStr
 template <typename S, typename R>
 cudaError_t launch_d2q9_step(const D2Args<S, R>& a, int variant, bool general, int nblocks, cudaStream_t st);
 
-// Tile shape of a kernel variant.
+// Tile shape of a kernel variant.  Variants 0-3 are tile kernels (32x8,
+// 32x4, 64x4, 32x16); variant 4 tiles like variant 0 and runs the interior
+// tiles of FP32 contexts through the column-marching kernel.
 void d2q9_variant_tile(int variant, int* tx, int* ty);
 int d2q9_num_variants();
+constexpr int D2Q9_MARCH_VARIANT = 4;
+// The tile-kernel variant that serves `variant` (4 -> 0).
+inline int d2q9_tile_kernel_variant(int variant) { return variant == D2Q9_MARCH_VARIANT ? 0 : variant; }
+
+// Column-marching step over runs of interior tiles (lbm_d2q9_march.cu).
+// runs[r] = {bx | by0 << 16, tiles, first entry in run_flags, 0}; tmap is a
+// CUtensorMap over a.fin viewed as [18][ny][pitch] floats with a
+// 44 x 10 x 18 box.  Status bit 2 is set if a bulk-copy wait runs out.
+size_t d2q9_march_smem_bytes();
+cudaError_t launch_d2q9_march(const D2Args<float, float>& a, const void* tmap, const int4* runs,
+                              const uint8_t* run_flags, int nruns, cudaStream_t st);
+constexpr int D2Q9_MARCH_BOX_W = 44, D2Q9_MARCH_BOX_H = 10;
 
 // FP64 diagnostics over the current populations and macro buffer:
 // per-block partials [nblocks][3] = mass1, mass2, max |u|^2.

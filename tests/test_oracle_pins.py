@@ -689,3 +689,42 @@ def test_laplace_law_linear_in_inverse_radius():
     assert gamma > 0
     assert r2 > 0.999
     assert abs(icpt) < 0.05 * max(dps)
+
+
+def _outlet_identity_error(o, w):
+    """max |u_x(x_N) - chi u_x(x_{N-1})| with chi = Q_in / Q_out formed from
+    the reported fields themselves (Eq. 23 over x1 and x_{N-1})."""
+    rho, u, _ = o.macros()
+    fl = slice(w.cfg["faces"][0]["lo"], w.cfg["faces"][0]["hi"] + 1)
+    nx = w.cfg["nx"]
+    rt = rho[0] + rho[1]
+    qin = (rt[fl, 0] * u[0][fl, 0]).sum()
+    qout = (rt[fl, nx - 2] * u[0][fl, nx - 2]).sum()
+    chi = qin / qout
+    return np.max(np.abs(u[0][fl, nx - 1] - chi * u[0][fl, nx - 2]))
+
+
+def test_same_step_chi_uses_the_steps_own_fluxes():
+    """Eq. 23 printed at t + dt: with the same-step timing, the outlet's
+    normal velocity is chi times that of x_{N-1} with chi formed from the
+    very fields the step reports; with the one-step lag it is not."""
+    w = _small_channel()
+    same = O.Oracle2D(dict(w.cfg, chi_same_step=1), w.solid, w.rho, w.u)
+    lag = O.Oracle2D(w.cfg, w.solid, w.rho, w.u)
+    same.step(40)
+    lag.step(40)
+    assert _outlet_identity_error(same, w) < 1e-15
+    assert _outlet_identity_error(lag, w) > 1e-9
+
+
+def test_lagged_and_same_step_chi_agree_at_steady_state():
+    """Both timings of chi lead to the same steady single-phase channel
+    flow (chi -> 1, where the lag no longer matters)."""
+    out = {}
+    for same in (0, 1):
+        w = W.channel(nx=40, ny=14, u_max=0.02, G12=0.0, Gw=(0, 0), nu=(1 / 6, 1 / 6), droplet=False)
+        o = O.Oracle2D(dict(w.cfg, chi_same_step=same), w.solid, w.rho, w.u, threads=4)
+        o.step(4000)
+        out[same] = (o.macros()[1], o.scalars()["chi"])
+    assert abs(out[0][1] - 1.0) < 1e-2 and abs(out[1][1] - 1.0) < 1e-2
+    assert np.max(np.abs(out[0][0] - out[1][0])) / np.max(np.abs(out[1][0])) < 1e-4
