@@ -29,7 +29,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-KERNEL_SRC = os.path.join(ROOT, "paper_2512_12934_gb300", "csrc", "lbm_d2q9.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2512_12934_gb300", "csrc", f)
+              for f in ("lbm_d2q9.cu", "d2q9_tile.cuh", "lbm_internal.h")]
 KERNEL_SRC_3D = os.path.join(ROOT, "paper_2512_12934_gb300", "csrc", "lbm_d3q19.cu")
 PROFILE_SUMMARY_3D = os.path.join(ROOT, "profiles", "d3q19_step_coflow_512x96x96.md")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "d2q9_step_channel_1024x128.md")
@@ -64,6 +65,8 @@ def parse():
     p.add_argument("--hbm-nx", type=int, default=8192, help="x extent of the HBM-resident channel grid")
     p.add_argument("--hbm-ny", type=int, default=2048, help="y extent of the HBM-resident channel grid")
     p.add_argument("--lbm-steps-3d", type=int, default=200, help="D3Q19 time steps per benchmark step")
+    p.add_argument("--tile-variant", type=int, default=-1,
+                   help="tile variant of the channel solver (default: the library's choice for the grid)")
     return p.parse_args()
 
 
@@ -162,13 +165,23 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_hash(paths):
+    """First 16 hex digits of the SHA-256 of the kernel's source files, read
+    in order (a profile summary records it; counters apply only while the
+    source is unchanged)."""
+    h = hashlib.sha256()
+    for p in (paths if isinstance(paths, (list, tuple)) else [paths]):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic():
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source; else None."""
     if not os.path.exists(PROFILE_SUMMARY):
         return None
     text = open(PROFILE_SUMMARY).read()
-    h = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash(KERNEL_SRC)
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_traffic = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
     if not m_hash or not m_traffic or m_hash.group(1) != h:
@@ -182,7 +195,7 @@ def profiled_traffic_3d():
     if not os.path.exists(PROFILE_SUMMARY_3D):
         return None
     text = open(PROFILE_SUMMARY_3D).read()
-    h = hashlib.sha256(open(KERNEL_SRC_3D, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash(KERNEL_SRC_3D)
     m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_traffic = re.search(r"dram_bytes_per_step_full_size:\s*([0-9.eE+]+)", text)
     if not m_hash or not m_traffic or m_hash.group(1) != h:
@@ -691,6 +704,8 @@ def main():
     w = W.channel() if args.workload == "channel" else W.channel(nx=args.hbm_nx, ny=args.hbm_ny, R=240, xc=1600)
     S = args.lbm_steps
     solver = lbm.Solver(w.cfg, w.solid, w.rho, w.u, precision=args.precision, stream=stream.cuda_stream)
+    if args.tile_variant >= 0:
+        solver.set_tile_variant(args.tile_variant)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     rho_h = np.ascontiguousarray(w.rho, dtype=np.float64)
     u_h = np.ascontiguousarray(w.u, dtype=np.float64)

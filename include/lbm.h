@@ -243,6 +243,20 @@ lbm_status lbm_tile_stats(lbm_ctx* ctx, int* variant, int* fast_tiles, int* gene
  * first use); 0 launches every step individually.  Results are identical. */
 lbm_status lbm_set_graph_mode(lbm_ctx* ctx, int use_graphs);
 
+/* Timing of chi, the outlet mass-flux correction (Eqs. 22, 23).
+ *  same_step = 0 (default): chi of a step comes from the previous step's
+ *    inlet and outlet fluxes (one-step lag), so each step needs no grid-wide
+ *    sum before its collisions.
+ *  same_step = 1: chi comes from the step's own fluxes, as Eq. 23 is printed
+ *    (t + dt): after the general tiles of each step one more launch sums the
+ *    step's FP64 flux partials, sets the outlet nodes' normal velocity
+ *    (Eq. 22) and collides them.  lambda (Eq. 21) stays lagged in both: Eq.
+ *    20 needs it before the step's velocities exist.
+ * No effect without an outlet carrying the chi correction.  FP32 and FP64
+ * storage, graph schedule, contexts outside batches; LBM_ERR_UNSUPPORTED
+ * otherwise.  Waits for the context's stream. */
+lbm_status lbm_set_chi_timing(lbm_ctx* ctx, int same_step);
+
 /* Schedule of lbm_step for this context: LBM_SCHEDULE_GRAPHS (default) or
  * LBM_SCHEDULE_PERSISTENT (FP32 storage only; see lbm_batch_set_schedule,
  * of which this is the one-member case).  Under the persistent schedule

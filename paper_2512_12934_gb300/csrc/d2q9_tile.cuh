@@ -559,22 +559,30 @@ struct LamFold {
     double valid;
 };
 
+// part / scal: the partials and scalar block to fold (those of the previous
+// step, a.part_in / a.scal_in, for the lagged lambda and chi).
+template <typename S, typename R>
+__device__ __forceinline__ void fold_begin(const D2Args<S, R>& a, LamFold& L, const double* part,
+                                           const double* scal) {
+    const int lane = threadIdx.x & 31, j = lane >> 3, c = lane & 7;
+    L.valid = ld_mut(scal + 5);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) L.p[k] = c + 8 * k < a.nslots ? ld_mut(part + (c + 8 * k) * 4 + j) : 0.0;
+}
 template <typename S, typename R>
 __device__ __forceinline__ void fold_begin(const D2Args<S, R>& a, LamFold& L) {
-    const int lane = threadIdx.x & 31, j = lane >> 3, c = lane & 7;
-    L.valid = ld_mut(a.scal_in + 5);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) L.p[k] = c + 8 * k < a.nslots ? ld_mut(a.part_in + (c + 8 * k) * 4 + j) : 0.0;
+    fold_begin(a, L, a.part_in, a.scal_in);
 }
 
 template <typename S, typename R>
-__device__ __forceinline__ void fold_finish(const D2Args<S, R>& a, const LamFold& L, double& lam, double& chi) {
+__device__ __forceinline__ void fold_finish(const D2Args<S, R>& a, const LamFold& L, double& lam, double& chi,
+                                            const double* part, const double* scal) {
     const int lane = threadIdx.x & 31, j = lane >> 3, c = lane & 7;
     double t = 0.0;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         if (c + 8 * k < a.nslots) t += L.p[k];
-    for (int sl = c + 64; sl < a.nslots; sl += 8) t += ld_mut(a.part_in + sl * 4 + j);
+    for (int sl = c + 64; sl < a.nslots; sl += 8) t += ld_mut(part + sl * 4 + j);
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
     double T[4];
@@ -582,13 +590,17 @@ __device__ __forceinline__ void fold_finish(const D2Args<S, R>& a, const LamFold
     for (int q = 0; q < 4; ++q) T[q] = __shfl_sync(0xffffffffu, t, 8 * q);
     // the quotients are taken in the tile's arithmetic precision R, which
     // is where lambda and chi are used
-    lam = ld_mut(a.scal_in + 0);
-    chi = ld_mut(a.scal_in + 1);
+    lam = ld_mut(scal + 0);
+    chi = ld_mut(scal + 1);
     if (L.valid != 0.0 && a.out_face >= 0 && T[3] > 0.0) {
         const R um = R(T[2]) / R(T[3]);
         lam = um > R(0) ? double(um) : 0.0;
         chi = (!a.have_inlet || fabs(T[1]) < 1e-14) ? 1.0 : double(R(T[0]) / R(T[1]));
     }
+}
+template <typename S, typename R>
+__device__ __forceinline__ void fold_finish(const D2Args<S, R>& a, const LamFold& L, double& lam, double& chi) {
+    fold_finish(a, L, lam, chi, a.part_in, a.scal_in);
 }
 
 template <typename S, typename R, int TX, int TY>
@@ -1186,6 +1198,7 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
     }
 
     // ---- Eq. 22: outlet normal velocity = chi * u_n(x_{N-1}), same row ----
+    R un_nbr = R(0);  // normal velocity of x_{N-1}, same row (outlet nodes)
     if (GEN && a.out_face >= 0) {
         const FaceDev& OF = a.face[a.out_face];
         bool covers;
@@ -1199,8 +1212,9 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
             tile_sync<GEN, NT>();
             if (fluid && own_face == a.out_face) {
                 const R chi = sm.chi;
-                if (OF.side <= 1) ux = chi * sm.un[along];
-                else uy = chi * sm.un[along];
+                un_nbr = sm.un[along];
+                if (OF.side <= 1) ux = chi * un_nbr;
+                else uy = chi * un_nbr;
             }
         }
     }
@@ -1229,7 +1243,30 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
             R* Fp = a.Fp_out + (F.base + ((F.side <= 1) ? y : x) - F.lo) * 8 + 4;
             Fp[0] = Fx0; Fp[1] = Fy0; Fp[2] = Fx1; Fp[3] = Fy1;
         }
-        if (a.macro) {
+        bool defer = false;
+        if constexpr (GEN) {
+            if (a.oc_save && own_face >= 0 && own_face == a.out_face && a.face[own_face].chi) {
+                // chi from this step's flux sums (Eq. 23 at t + dt): the outlet
+                // node's collision waits for them in d2q9_outlet_chi_kernel
+                const FaceDev& F = a.face[own_face];
+                R* q = a.oc_save + (size_t)(F.base + ((F.side <= 1) ? y : x) - F.lo) * OC_STRIDE;
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) q[k * 9 + i] = f[k][i];
+                q[18] = rho0;
+                q[19] = rho1;
+                q[20] = Fx0;
+                q[21] = Fy0;
+                q[22] = Fx1;
+                q[23] = Fy1;
+                q[24] = (F.side <= 1) ? uy : ux;  // tangential velocity
+                q[25] = un_nbr;
+                q[26] = R(1);                     // written this step
+                defer = true;
+            }
+        }
+        if (a.macro && !defer) {
             a.macro[n] = rho0;
             a.macro[a.plane + n] = rho1;
             a.macro[2 * a.plane + n] = ux;
@@ -1239,7 +1276,9 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
         // General tiles (latency-bound) run both components through packed
         // FP32x2 operations; fast tiles (issue- and HBM-bound) measured faster
         // with the scalar form.
-        if constexpr (GEN && std::is_same<R, float>::value) {
+        if (defer) {
+            // collided by d2q9_outlet_chi_kernel
+        } else if constexpr (GEN && std::is_same<R, float>::value) {
             R o2[2][9];
             collide_pair(a, f, rho0, rho1, ux, uy, Fx0, Fy0, Fx1, Fy1, o2);
 #pragma unroll

@@ -109,6 +109,10 @@ struct lbm_ctx {
     void* stage = nullptr;             // pinned staging buffer for host transfers
     size_t stage_bytes = 0;
     int timing_every = 0;
+    // same-step chi (Eq. 23 at t + dt): outlet-node state between the general
+    // tiles and d2q9_outlet_chi_kernel, [slot][OC_STRIDE]
+    int chi_same_step = 0;
+    void* oc_state = nullptr;
     // persistent schedule of a single context: a batch of one member
     int schedule = LBM_SCHEDULE_GRAPHS;
     lbm_batch* solo = nullptr;
@@ -154,7 +158,7 @@ void free_ctx(lbm_ctx* c) {
     for (cudaEvent_t e : c->ev_start) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_mid) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
-    void* ptrs[] = {c->march_runs, c->march_flags, c->f[0], c->f[1], c->info, c->blocks, c->block_flags, c->block_strips, c->uin, c->Fp[0], c->Fp[1], c->fo[0], c->fo[1],
+    void* ptrs[] = {c->oc_state, c->march_runs, c->march_flags, c->f[0], c->f[1], c->info, c->blocks, c->block_flags, c->block_strips, c->uin, c->Fp[0], c->Fp[1], c->fo[0], c->fo[1],
                     c->scal[0], c->scal[1], c->partials[0], c->partials[1], c->block_slot, c->status,
                     c->macro, c->diag_partials, c->rref[0], c->rref[1]};
     for (void* p : ptrs)
@@ -202,6 +206,7 @@ D2Args<S, R> make_args_par(lbm_ctx* c, int in, bool write_macros) {
     a.rref_in = c->rref[in];
     a.rref_out = c->rref[out];
     a.status = c->status;
+    a.oc_save = (c->chi_same_step && c->oc_state) ? static_cast<R*>(c->oc_state) : nullptr;
     a.G12 = (R)c->params.G12;
     a.Gw[0] = (R)c->params.Gw[0];
     a.Gw[1] = (R)c->params.Gw[1];
@@ -234,7 +239,11 @@ cudaError_t launch_lists(lbm_ctx* c, bool macros, cudaStream_t st, cudaStream_t 
     // SMs they start at once instead of waiting for fast CTAs to drain.
     D2Args<S, R> ag = a;
     ag.list_off = c->nfast;
+    // same-step chi: the outlet nodes are collided after the general tiles
+    // (on their stream), once the step's flux partials exist
+    const bool chi_same = a.oc_save != nullptr;
     if (fork && e == cudaSuccess) e = launch_d2q9_step<S, R>(ag, c->variant, true, c->ngeneral, side);
+    if (fork && chi_same && e == cudaSuccess) e = launch_d2q9_outlet_chi<S, R>(a, side);
     if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
         if (e == cudaSuccess && c->nmarch > 0)
             e = launch_d2q9_march(a, &c->tmap[c->cur], c->march_runs, c->march_flags, c->nmarch, st);
@@ -242,6 +251,7 @@ cudaError_t launch_lists(lbm_ctx* c, bool macros, cudaStream_t st, cudaStream_t 
     if (e == cudaSuccess) e = launch_d2q9_step<S, R>(a, c->variant, false, c->nfast, st);
     if (e == cudaSuccess && mid) e = cudaEventRecord(mid, st);
     if (!fork && e == cudaSuccess) e = launch_d2q9_step<S, R>(ag, c->variant, true, c->ngeneral, st);
+    if (!fork && chi_same && e == cudaSuccess) e = launch_d2q9_outlet_chi<S, R>(a, st);
     if (fork && e == cudaSuccess) {
         e = cudaEventRecord(c->ev_join, side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join, 0);
@@ -256,7 +266,7 @@ lbm_status launch_one(lbm_ctx* c, bool macros, cudaStream_t st, cudaEvent_t mid 
     // the ping-pong slot written by this step becomes current
     c->cur = 1 - c->cur;
     c->step += 1;
-    c->launches += (c->nfast > 0) + (c->ngeneral > 0) + (c->nmarch > 0);
+    c->launches += (c->nfast > 0) + (c->ngeneral > 0) + (c->nmarch > 0) + (c->chi_same_step ? 1 : 0);
     return LBM_OK;
 }
 
@@ -301,7 +311,8 @@ lbm_status run_plain(lbm_ctx* c, int64_t cnt) {
         cudaError_t e = cudaGraphLaunch(c->gexec[c->cur], c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "step graph launch");
         c->step += kGraphSteps;
-        c->launches += (int64_t)kGraphSteps * ((c->nfast > 0) + (c->ngeneral > 0) + (c->nmarch > 0));
+        c->launches += (int64_t)kGraphSteps *
+                       ((c->nfast > 0) + (c->ngeneral > 0) + (c->nmarch > 0) + (c->chi_same_step ? 1 : 0));
         cnt -= kGraphSteps;
     }
     for (; cnt > 0; --cnt) {
@@ -1623,8 +1634,33 @@ lbm_status lbm_set_schedule(lbm_ctx* c, int schedule) {
         return fail(c, LBM_ERR_INVALID_ARG, "unknown schedule");
     if (schedule == LBM_SCHEDULE_PERSISTENT && c->precision != LBM_FP32)
         return fail(c, LBM_ERR_UNSUPPORTED, "the persistent schedule is built for FP32 storage only");
+    if (schedule == LBM_SCHEDULE_PERSISTENT && c->chi_same_step)
+        return fail(c, LBM_ERR_UNSUPPORTED, "the persistent schedule runs the lagged chi only");
     CK(cudaStreamSynchronize(c->stream));
     c->schedule = schedule;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_chi_timing(lbm_ctx* c, int same_step) {
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
+    if (same_step && c->precision == LBM_FP32_FP16STORE)
+        return fail(c, LBM_ERR_UNSUPPORTED, "same-step chi is built for FP32 and FP64 storage");
+    if (same_step && c->schedule == LBM_SCHEDULE_PERSISTENT)
+        return fail(c, LBM_ERR_UNSUPPORTED, "the persistent schedule runs the lagged chi only");
+    CK(cudaStreamSynchronize(c->stream));
+    const bool on = same_step && c->out_face >= 0 && c->faces[c->out_face].chi;
+    if (on && !c->oc_state) {
+        const size_t bytes = (size_t)std::max(1, c->nface_nodes) * OC_STRIDE * c->rbytes;
+        CK(cudaMalloc(&c->oc_state, bytes));
+        CK(cudaMemset(c->oc_state, 0, bytes));
+    }
+    c->chi_same_step = on ? 1 : 0;
+    for (int p = 0; p < 2; ++p)  // captured steps carry the old launch sequence
+        if (c->gexec[p]) {
+            cudaGraphExecDestroy(c->gexec[p]);
+            c->gexec[p] = nullptr;
+        }
     return LBM_OK;
 }
 
@@ -1871,6 +1907,8 @@ lbm_status lbm_batch_create(lbm_ctx* const* members, int n, void* cuda_stream, l
         if (!members[i]) return bfail(nullptr, LBM_ERR_INVALID_ARG, "NULL member");
         if (members[i]->precision != members[0]->precision)
             return bfail(nullptr, LBM_ERR_INVALID_ARG, "members must share one precision");
+        if (members[i]->chi_same_step)
+            return bfail(nullptr, LBM_ERR_UNSUPPORTED, "batches run the lagged chi only (lbm_set_chi_timing)");
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return bfail(nullptr, LBM_ERR_INVALID_ARG, "a member appears twice");
     }

@@ -63,7 +63,58 @@ __global__ void __maxnreg__((gen_maxreg<R, TX, TY, ROLES>())) d2q9_batch_general
     batch_tile<S, R, TX, TY, true, ROLES>(b);
 }
 
-// FP64 mass / speed reduction for diagnostics.
+// Same-step chi (Eq. 23 at t + dt).  Runs after the general tiles of the
+// step, which left the outlet nodes' post-stream state in a.oc_save and this
+// step's FP64 flux partials in a.part_out.  Warp 0 folds the partials in the
+// fixed order of the lagged fold; then every outlet node gets its normal
+// velocity chi * u_n(x_{N-1}) (Eq. 22), is collided (Eq. 1) and stored.
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) d2q9_outlet_chi_kernel(const __grid_constant__ D2Args<S, R> a) {
+    __shared__ R s_chi;
+    if (threadIdx.x < 32) {
+        LamFold L;
+        fold_begin(a, L, a.part_out, a.scal_out);
+        double lam, chi;
+        fold_finish(a, L, lam, chi, a.part_out, a.scal_out);
+        if (threadIdx.x == 0) s_chi = R(chi);
+    }
+    __syncthreads();
+    const R chi = s_chi;
+    const FaceDev& F = a.face[a.out_face];
+    const int len = F.hi - F.lo + 1;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        const R* q = a.oc_save + (size_t)(F.base + t) * OC_STRIDE;
+        if (q[26] == R(0)) continue;  // a solid node of the face: never written
+        const int x = F.side == 0 ? 0 : (F.side == 1 ? a.nx - 1 : F.lo + t);
+        const int y = F.side == 2 ? 0 : (F.side == 3 ? a.ny - 1 : F.lo + t);
+        const int n = y * a.pitch + x;
+        R f[2][9];
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[k][i] = q[k * 9 + i];
+        const R rho0 = q[18], rho1 = q[19];
+        const R un = chi * q[25], ut = q[24];
+        const R ux = F.side <= 1 ? un : ut, uy = F.side <= 1 ? ut : un;
+        if (a.macro) {
+            a.macro[n] = rho0;
+            a.macro[a.plane + n] = rho1;
+            a.macro[2 * a.plane + n] = ux;
+            a.macro[3 * a.plane + n] = uy;
+        }
+        const R uu3 = R(3) * (ux * ux + uy * uy);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            R o[9];
+            collide_scalar<R>(a.s[k], k == 0 ? rho0 : rho1, q[20 + 2 * k], q[21 + 2 * k], ux, uy, uu3, f[k], o);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Pop<S, R>::st(a.fout, (k * 9 + i) * a.plane + n, o[i], R(0));
+        }
+        if (!isfinite(rho0 + rho1 + ux + uy)) atomicOr(a.status, 1u);
+    }
+}
+
+// FP64 mass / speed reduction for diagnostics.// FP64 mass / speed reduction for diagnostics.
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) d2q9_diag_kernel(const S* __restrict__ f, const R* __restrict__ macro,
                                                         const uint16_t* __restrict__ info,
@@ -214,6 +265,16 @@ cudaError_t launch_d2q9_step(const D2Args<S, R>& a, int variant, bool general, i
 }
 
 template <typename S, typename R>
+cudaError_t launch_d2q9_outlet_chi(const D2Args<S, R>& a, cudaStream_t st) {
+    if constexpr (std::is_same<S, __half>::value) {
+        return cudaErrorNotSupported;
+    } else {
+        d2q9_outlet_chi_kernel<S, R><<<1, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+}
+
+template <typename S, typename R>
 cudaError_t launch_d2q9_diag(const S* f, const R* macro, const uint16_t* info, const void* rref, int nx,
                              int ny, int px, int py, int pitch, long long plane, double* partials, int nblocks,
                              cudaStream_t st) {
@@ -227,6 +288,9 @@ template cudaError_t launch_d2q9_batch<__half, float>(const BatchArgs<__half, fl
 template cudaError_t launch_d2q9_step<float, float>(const D2Args<float, float>&, int, bool, int, cudaStream_t);
 template cudaError_t launch_d2q9_step<double, double>(const D2Args<double, double>&, int, bool, int, cudaStream_t);
 template cudaError_t launch_d2q9_step<__half, float>(const D2Args<__half, float>&, int, bool, int, cudaStream_t);
+template cudaError_t launch_d2q9_outlet_chi<float, float>(const D2Args<float, float>&, cudaStream_t);
+template cudaError_t launch_d2q9_outlet_chi<double, double>(const D2Args<double, double>&, cudaStream_t);
+template cudaError_t launch_d2q9_outlet_chi<__half, float>(const D2Args<__half, float>&, cudaStream_t);
 template cudaError_t launch_d2q9_diag<float, float>(const float*, const float*, const uint16_t*, const void*, int,
                                                     int, int, int, int, long long, double*, int, cudaStream_t);
 template cudaError_t launch_d2q9_diag<double, double>(const double*, const double*, const uint16_t*, const void*,

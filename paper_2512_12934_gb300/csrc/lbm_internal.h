@@ -30,6 +30,8 @@ constexpr unsigned BLOCK_SOLID = 2u;    // a solid site lies within the tile's p
 constexpr unsigned BLOCK_GENERAL = 4u;  // general list
 constexpr unsigned BLOCK_LAMBDA = 8u;   // general tile that needs lambda / chi (sees outlet face nodes)
 
+constexpr int OC_STRIDE = 28;  // saved outlet-node state: f[18], rho[2], F[4], u_t, u_n(x_{N-1}), written flag
+
 constexpr int FACE_INLET = 1;
 constexpr int FACE_OUTLET = 2;
 
@@ -81,6 +83,10 @@ struct D2Args {
     const void* __restrict__ rref_in;     // FP16 storage: [2][plane] half reference densities (decode)
     void* __restrict__ rref_out;          // FP16 storage: reference densities written by this step
     unsigned int* status;
+    // same-step chi (Eq. 23 at t + dt): per outlet slot, the state of the
+    // outlet node saved for d2q9_outlet_chi_kernel (OC_STRIDE values); NULL
+    // for the lagged chi
+    R* __restrict__ oc_save;
     R G12;
     R Gw[2];
     R s[2][9];
@@ -137,6 +143,13 @@ cudaError_t launch_d2q9_persist(const PersistArgs<S, R>& p, int variant, cudaStr
 // true -> general kernel; nblocks list entries starting at a.list_off.
 template <typename S, typename R>
 cudaError_t launch_d2q9_step(const D2Args<S, R>& a, int variant, bool general, int nblocks, cudaStream_t st);
+
+// Same-step chi: after the general tiles of a step, fold that step's flux
+// partials into chi (Eq. 23 at t + dt), set the outlet nodes' normal
+// velocity (Eq. 22), collide them and store their populations (FP32 and
+// FP64 storage).
+template <typename S, typename R>
+cudaError_t launch_d2q9_outlet_chi(const D2Args<S, R>& a, cudaStream_t st);
 
 // Tile shape of a kernel variant.  Variants 0-3 are tile kernels (32x8,
 // 32x4, 64x4, 32x16); variant 4 tiles like variant 0 and runs the interior

@@ -113,6 +113,8 @@ def load():
     L.lbm_tile_stats.argtypes = [c_ctx] + [ctypes.POINTER(ctypes.c_int)] * 3 + [ctypes.POINTER(ctypes.c_int64)] * 2
     L.lbm_set_graph_mode.restype = ctypes.c_int
     L.lbm_set_graph_mode.argtypes = [c_ctx, ctypes.c_int]
+    L.lbm_set_chi_timing.restype = ctypes.c_int
+    L.lbm_set_chi_timing.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_set_schedule.restype = ctypes.c_int
     L.lbm_set_schedule.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_mass_noalloc.restype = ctypes.c_int
@@ -347,6 +349,11 @@ class Solver:
     def set_schedule(self, name):
         """'graphs' (default) or 'persistent' (lbm_set_schedule)."""
         _check(load().lbm_set_schedule(self.h, SCHEDULES[name]), self.h)
+
+    def set_chi_timing(self, same_step):
+        """chi from the step's own fluxes (True) or the previous step's
+        (False, default): lbm_set_chi_timing."""
+        _check(load().lbm_set_chi_timing(self.h, int(bool(same_step))), self.h)
 
     def autotune(self, steps=20):
         v = ctypes.c_int()
