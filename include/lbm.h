@@ -243,6 +243,18 @@ lbm_status lbm_tile_stats(lbm_ctx* ctx, int* variant, int* fast_tiles, int* gene
  * first use); 0 launches every step individually.  Results are identical. */
 lbm_status lbm_set_graph_mode(lbm_ctx* ctx, int use_graphs);
 
+/* Moving wall beyond a closed y edge (side LBM_YMIN: the halfway wall at
+ * y = -1/2, LBM_YMAX: at y = ny - 1/2) with x-velocity ux (|ux| <= 0.2;
+ * 0 = at rest, the default).  The paper shears droplets between plates
+ * moving in opposite directions (Taylor deformation, Sec. III A) without
+ * giving the wall scheme; here a population reflected at the wall gains
+ * 2 w_i rho_k (e_i . u_w) / c_s^2, rho_k the node's own density before
+ * streaming (halfway bounce-back with the wall's momentum), which keeps
+ * plane Couette flow exact.  Needs a non-periodic y axis without an open
+ * face on that side; FP32 and FP64 storage.  Applies from the next step
+ * (a running batch picks it up when rebuilt).  Waits for the stream. */
+lbm_status lbm_set_wall_velocity(lbm_ctx* ctx, int side, double ux);
+
 /* Timing of chi, the outlet mass-flux correction (Eqs. 22, 23).
  *  same_step = 0 (default): chi of a step comes from the previous step's
  *    inlet and outlet fluxes (one-step lag), so each step needs no grid-wide

@@ -206,6 +206,7 @@ typedef struct {
     int use_s_full;   /* 1: S taken verbatim from s_full (textbook reductions) */
     double s_full[2][NQ];
     int chi_same_step; /* 1: chi of Eq. 23 from this step's fields (t + dt, as printed); 0: lagged */
+    double wall_ux[2];  /* x-velocity of the walls beyond the closed edges y = 0 and y = ny-1 */
 } orc_params;
 
 typedef struct {
@@ -506,6 +507,19 @@ static void one_step(orc_state* st) {
                 int blocked = pull_site(st, x - EXV[i], y - EYV[i], &ns);
                 for (int k = 0; k < NCOMP; ++k)
                     fp[FIDX(k, i, n)] = blocked ? f[FIDX(k, opp[i], n)] : f[FIDX(k, i, ns)];
+                /* moving wall beyond a closed y edge (halfway bounce-back with
+                 * the wall's momentum): f_i += 2 w_i rho_k (e_i . u_w) / c_s^2,
+                 * rho_k the node's own density (its post-collision sum) */
+                const int sy = y - EYV[i];
+                if (blocked && !st->p.periodic_y && (sy < 0 || sy >= ny)) {
+                    const double uw = st->p.wall_ux[sy < 0 ? 0 : 1];
+                    if (uw != 0.0)
+                        for (int k = 0; k < NCOMP; ++k) {
+                            double rk = 0.0;
+                            for (int j = 0; j < NQ; ++j) rk += f[FIDX(k, j, n)];
+                            fp[FIDX(k, i, n)] += 2.0 * omega_of(i) * rk * (EXV[i] * uw) / CS2;
+                        }
+                }
             }
         }
 

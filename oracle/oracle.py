@@ -52,6 +52,12 @@ Readings taken where the paper is silent, garbled or inconsistent:
     open face: x = -1 -> x1, x = -2 -> x2, and likewise at the far side.
 13. Initial state f = feq(rho_k, u_init); the macroscopic fields reported
     after n steps are those the n-th collision used.
+14. Moving walls (the Taylor deformation test of Sec. III A shears a
+    droplet between plates moving in opposite directions; the paper does not
+    give the wall scheme): cfg["wall_ux"] = (u_bottom, u_top) moves the
+    walls beyond the closed edges y = 0 and y = ny - 1 along x.  A
+    population reflected there gains 2 w_i rho_k (e_i . u_w) / c_s^2, with
+    rho_k the node's own density (sum of its post-collision populations).
 """
 import ctypes
 import os
@@ -71,6 +77,7 @@ class _Params(ctypes.Structure):
         ("s_e", ctypes.c_double), ("s_q", ctypes.c_double), ("s_eps_mode", ctypes.c_int),
         ("body", ctypes.c_double * 2), ("use_s_full", ctypes.c_int),
         ("s_full", (ctypes.c_double * 9) * 2), ("chi_same_step", ctypes.c_int),
+        ("wall_ux", ctypes.c_double * 2),
     ]
 
 
@@ -194,6 +201,8 @@ class Oracle2D:
         body = cfg.get("body", (0.0, 0.0))
         p.body[0], p.body[1] = body[0], body[1]
         p.chi_same_step = int(cfg.get("chi_same_step", 0))
+        wu = cfg.get("wall_ux", (0.0, 0.0))
+        p.wall_ux[0], p.wall_ux[1] = float(wu[0]), float(wu[1])
         sf = cfg.get("s_full")
         if sf is not None:
             p.use_s_full = 1

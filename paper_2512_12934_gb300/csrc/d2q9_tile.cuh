@@ -139,11 +139,21 @@ __device__ __forceinline__ R feq_(int i, R rho, R ux, R uy) {
 // f*_i(x - e_i); a set bit i in `info` means that source is solid or outside
 // a closed edge, and halfway bounce-back (Eq. B1) takes f*_opp(i)(x).
 
-// Interior pull: every source lies inside the grid, no wrap needed.
+// Interior pull: every source lies inside the grid, no wrap needed.  Nodes
+// without a solid neighbour (no bounce-back bit, the common case) take the
+// sources straight from their offsets.
 template <typename S, typename R>
 __device__ __forceinline__ void pull_interior(const D2Args<S, R>& a, int n, unsigned info, R (&f)[2][9]) {
     R ref[2];
     node_ref(a, n, ref);
+    if ((info & 0x1ffu) == 0u) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                f[k][i] = Pop<S, R>::ld(a.fin, (k * 9 + i) * a.plane + n - ex_(i) - ey_(i) * a.pitch, w_<R>(i) * ref[k]);
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const bool bb = (info >> i) & 1u;
@@ -177,6 +187,25 @@ __device__ __forceinline__ void pull_wrap(const D2Args<S, R>& a, int x, int y, u
 #pragma unroll
         for (int k = 0; k < 2; ++k)
             f[k][i] = Pop<S, R>::ld(a.fin, (k * 9 + dir) * a.plane + src, w_<R>(i) * ref[k]);
+    }
+    // Moving wall beyond a closed y edge (halfway bounce-back carrying the
+    // wall's momentum): a population reflected there gains
+    // 2 w_i rho_k (e_i . u_w) / c_s^2, rho_k the node's own density (the sum
+    // of its post-collision populations).  FP32 / FP64 storage.
+    if constexpr (!is_half_<S>()) {
+        const int side = y == 0 ? 0 : (y == a.ny - 1 ? 1 : -1);
+        if (a.wall_on && !a.py && side >= 0 && a.wall_ux[side] != R(0)) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                R rk = R(0);
+#pragma unroll
+                for (int j = 0; j < 9; ++j) rk += Pop<S, R>::ld(a.fin, (k * 9 + j) * a.plane + n, R(0));
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (((info >> i) & 1u) && (side == 0 ? ey_(i) > 0 : ey_(i) < 0))
+                        f[k][i] += R(6) * w_<R>(i) * rk * (R(ex_(i)) * a.wall_ux[side]);
+            }
+        }
     }
 }
 

@@ -113,6 +113,8 @@ struct lbm_ctx {
     // tiles and d2q9_outlet_chi_kernel, [slot][OC_STRIDE]
     int chi_same_step = 0;
     void* oc_state = nullptr;
+    // moving walls beyond the closed edges y = 0 / y = ny - 1 (x-velocity)
+    double wall_ux[2] = {0.0, 0.0};
     // persistent schedule of a single context: a batch of one member
     int schedule = LBM_SCHEDULE_GRAPHS;
     lbm_batch* solo = nullptr;
@@ -207,6 +209,9 @@ D2Args<S, R> make_args_par(lbm_ctx* c, int in, bool write_macros) {
     a.rref_out = c->rref[out];
     a.status = c->status;
     a.oc_save = (c->chi_same_step && c->oc_state) ? static_cast<R*>(c->oc_state) : nullptr;
+    a.wall_on = (c->wall_ux[0] != 0.0 || c->wall_ux[1] != 0.0) ? 1 : 0;
+    a.wall_ux[0] = (R)c->wall_ux[0];
+    a.wall_ux[1] = (R)c->wall_ux[1];
     a.G12 = (R)c->params.G12;
     a.Gw[0] = (R)c->params.Gw[0];
     a.Gw[1] = (R)c->params.Gw[1];
@@ -1638,6 +1643,25 @@ lbm_status lbm_set_schedule(lbm_ctx* c, int schedule) {
         return fail(c, LBM_ERR_UNSUPPORTED, "the persistent schedule runs the lagged chi only");
     CK(cudaStreamSynchronize(c->stream));
     c->schedule = schedule;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wall_velocity(lbm_ctx* c, int side, double ux) {
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
+    if (side != LBM_YMIN && side != LBM_YMAX) return fail(c, LBM_ERR_INVALID_ARG, "side must be LBM_YMIN or LBM_YMAX");
+    if (c->grid.periodic[1] || c->open_side[side])
+        return fail(c, LBM_ERR_INVALID_ARG, "a moving wall needs a closed (non-periodic, not open) y edge");
+    if (!std::isfinite(ux) || std::fabs(ux) > 0.2) return fail(c, LBM_ERR_INVALID_ARG, "wall speed must be finite and |u| <= 0.2");
+    if (ux != 0.0 && c->precision == LBM_FP32_FP16STORE)
+        return fail(c, LBM_ERR_UNSUPPORTED, "moving walls are built for FP32 and FP64 storage");
+    CK(cudaStreamSynchronize(c->stream));
+    c->wall_ux[side == LBM_YMIN ? 0 : 1] = ux;
+    for (int p = 0; p < 2; ++p)  // captured steps carry the old arguments
+        if (c->gexec[p]) {
+            cudaGraphExecDestroy(c->gexec[p]);
+            c->gexec[p] = nullptr;
+        }
     return LBM_OK;
 }
 

@@ -5,16 +5,19 @@
 // a time, one warp per row.  For every block of 8 rows a single TMA load
 // (cp.async.bulk.tensor, 3D box over [18 planes][10 rows][44 columns])
 // brings the post-collision populations of all 18 planes that the block's
-// pulls read into shared memory; the load of the next block is in flight
-// while the current one is processed (two buffers, one mbarrier each).  The
-// pull stream (Eq. 2) with halfway bounce-back (Eq. B1) then reads shared
-// memory only, the densities go into a rolling window of 12 rows x 36
-// columns (own columns plus the two-node halo of Eq. 10's stencil), and the
-// interaction forces (Eqs. 10, 11), velocities (Eqs. 7, 8) and the MRT
-// collision with forcing (Eq. 1) are those of the tile kernels (the same
-// inline functions).  Compared with a tile kernel, each population is read
-// from L2/HBM by one bulk copy instead of one 4-byte load per node and
-// direction, and the halo rows above and below a tile are not pulled again.
+// pulls read into shared memory; three buffers keep the copies of the next
+// two blocks in flight while a block is processed.  Each warp pulls its row
+// once (Eq. 2 with halfway bounce-back, Eq. B1, from shared memory), puts
+// the densities into a rolling window of 18 rows x 36 columns (own columns
+// plus the two-node halo of Eq. 10's stencil) and keeps the populations in
+// registers; it collides that row one block later, when the window holds
+// the two rows above it.  Forces (Eqs. 10, 11), velocities (Eqs. 7, 8) and
+// the MRT collision with forcing (Eq. 1) are those of the tile kernels (the
+// same inline functions).  Compared with a tile kernel, each population is
+// read from L2/HBM by one bulk copy instead of one 4-byte load per node and
+// direction, the loads of later blocks overlap the arithmetic of the
+// current one, and the halo rows above and below a tile are not pulled
+// again.
 //
 // Interior tiles only (the tile's pulls and psi halo stay inside the grid,
 // no open face within reach): edge and general tiles keep the tile kernels.
@@ -29,7 +32,8 @@ constexpr int MTX = 32;          // columns per CTA (a warp per row)
 constexpr int MRB = 8;           // rows per block (warps per CTA)
 constexpr int MBW = MTX + 12;    // box columns [xs, xs + MBW), xs = (x0 - 3) rounded down to a multiple of 4
 constexpr int MBH = MRB + 2;     // box rows: the sources of one block of pulls
-constexpr int MWR = MRB + 4;     // density window rows
+constexpr int MNB = 3;           // box buffers: the copy of block j + 2 is in flight while block j is processed
+constexpr int MWR = 2 * MRB + 2; // density window rows: a pulled block, the block being collided, two halo rows
 constexpr int MWC = MTX + 4;     // density window columns
 constexpr unsigned MBOX_BYTES = 18u * MBH * MBW * 4u;
 
@@ -41,11 +45,10 @@ struct alignas(128) MarchBox {
 static_assert(sizeof(MarchBox) % 128 == 0, "TMA buffers must stay 128-byte aligned");
 
 struct MarchSmem {
-    MarchBox box[2];              // at offset 0 of a 128-byte aligned base
-    float2 rr[MWR][MWC];          // (rho_1, rho_2) of window row (y - ys + 2) mod MWR
+    MarchBox box[MNB];            // at offset 0 of a 128-byte aligned base
+    float2 rr[MWR][MWC];          // (rho_1, rho_2) of grid row y in window row (y - ys + 2) mod MWR
     unsigned char sol[MWR][MWC];
-    float fsave[2][18][2][MTX];   // pulled populations of a block's last two rows, for the next block
-    unsigned long long bar[2];
+    unsigned long long bar[MNB];
     int ok;
 };
 
@@ -90,18 +93,19 @@ __device__ __forceinline__ void tma_load_box(float* dst, const CUtensorMap* map,
         : "memory");
 }
 
-// Issue the load of the source rows [row0, row0 + MBH) into buffer b.
-__device__ __forceinline__ void issue_box(MarchSmem& sm, const CUtensorMap* map, int b, int xs, int row0) {
-    // earlier generic-proxy reads of the buffer are ordered before the async copy
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(&sm.bar[b], MBOX_BYTES);
-    tma_load_box(&sm.box[b].v[0][0][0], map, xs, row0, &sm.bar[b]);
-}
-
-// Pull (Eq. 2 with Eq. B1) of node (x, y) from a box whose first row is
-// row0: f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) when bit i of info is set.
+// Pull (Eq. 2 with Eq. B1) of node (x, y) from the box in buffer b whose
+// first row is row0: f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) when bit i of
+// info is set.
 __device__ __forceinline__ void pull_box(const MarchSmem& sm, int b, int row0, int xs, int x, int y, unsigned info,
                                          float (&f)[2][9]) {
+    const float(*v)[MBH][MBW] = sm.box[b].v;
+    if ((info & 0x1ffu) == 0u) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) f[k][i] = v[k * 9 + i][y - ey_(i) - row0][x - ex_(i) - xs];
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const bool bb = (info >> i) & 1u;
@@ -109,65 +113,54 @@ __device__ __forceinline__ void pull_box(const MarchSmem& sm, int b, int row0, i
         const int sy = (bb ? y : y - ey_(i)) - row0;
         const int sx = (bb ? x : x - ex_(i)) - xs;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) f[k][i] = sm.box[b].v[k * 9 + dir][sy][sx];
+        for (int k = 0; k < 2; ++k) f[k][i] = v[k * 9 + dir][sy][sx];
     }
 }
 
-// Density pair and solid flag of node (x, y) into window row wr, column c.
-// save != nullptr: also keep its pulled populations in save[q][srow][lane].
+__device__ __forceinline__ int wrow_of(int y, int ys) { return (y - ys + 2 + MWR) % MWR; }
+
+// Density pair and solid flag of node (x, y) into window column c; the
+// pulled populations are left in f.
 __device__ __forceinline__ void density_node(MarchSmem& sm, const D2Args<float, float>& a, int b, int row0, int xs,
-                                             int x, int y, int wr, int c, float (*save)[2][MTX], int srow) {
+                                             int ys, int x, int y, int c, float (&f)[2][9]) {
     const unsigned info = __ldg(a.info + y * a.pitch + x);
     float r0 = 0.f, r1 = 0.f;
     unsigned char sol = 1;
     if (!(info & INFO_SOLID)) {
-        float f[2][9];
         pull_box(sm, b, row0, xs, x, y, info, f);
         r0 = rho_of(f[0]);
         r1 = rho_of(f[1]);
         sol = 0;
-        if (save)
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-                for (int i = 0; i < 9; ++i) save[k * 9 + i][srow][threadIdx.x & 31] = f[k][i];
     }
+    const int wr = wrow_of(y, ys);
     sm.rr[wr][c] = make_float2(r0, r1);
     sm.sol[wr][c] = sol;
 }
 
-// Window row of grid row y.
-__device__ __forceinline__ int wrow_of(int y, int ys) { return (y - ys + 2 + MWR) % MWR; }
-
-// Densities of `nrows` rows from y_first: warp w takes row y_first + w
-// (own columns); warp `hw` then takes all their halo columns x0 - 2, x0 - 1,
-// x0 + 32, x0 + 33 in one pass (4 x nrows <= 32 nodes).
-__device__ __forceinline__ void density_rows(MarchSmem& sm, const D2Args<float, float>& a, int b, int row0, int xs,
-                                             int x0, int ys, int y_first, int nrows, int hw, float (*save)[2][MTX],
-                                             int save_from) {
+// Halo columns x0 - 2, x0 - 1, x0 + 32, x0 + 33 of `nrows` rows from
+// y_first, all taken by warp hw in one pass (4 x nrows <= 32 nodes).
+__device__ __forceinline__ void halo_columns(MarchSmem& sm, const D2Args<float, float>& a, int b, int row0, int xs,
+                                             int x0, int ys, int y_first, int nrows, int hw) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w < nrows) {
-        const int y = y_first + w;
-        density_node(sm, a, b, row0, xs, x0 + lane, y, wrow_of(y, ys), lane + 2, w >= save_from ? save : nullptr,
-                     w - save_from);
-    }
     if (w == hw && lane < 4 * nrows) {
         const int c4 = lane & 3, y = y_first + (lane >> 2);
         const int c = c4 < 2 ? c4 : MTX + c4;
-        density_node(sm, a, b, row0, xs, x0 - 2 + c, y, wrow_of(y, ys), c, nullptr, 0);
+        float f[2][9];
+        density_node(sm, a, b, row0, xs, ys, x0 - 2 + c, y, c, f);
     }
 }
 
 // Forces, velocity, collision and store of node (x0 + lane, y) whose
 // post-stream populations are f.
 __device__ __forceinline__ void collide_node(const MarchSmem& sm, const D2Args<float, float>& a, int x0, int ys,
-                                             int y, unsigned info, bool solid_near, const float (&f)[2][9]) {
+                                             int y, bool solid_near, const float (&f)[2][9]) {
     const int lane = threadIdx.x & 31;
     const int x = x0 + lane;
-    const bool fluid = !(info & INFO_SOLID);
+    const int n = y * a.pitch + x;
     int wrow[5];
 #pragma unroll
     for (int d = 0; d < 5; ++d) wrow[d] = wrow_of(y - 2 + d, ys);  // window rows of y - 2 ... y + 2
+    const bool fluid = sm.sol[wrow[2]][lane + 2] == 0;
     const float2 own = sm.rr[wrow[2]][lane + 2];
     const float rho0 = own.x, rho1 = own.y;
     float ux = 0.f, uy = 0.f;
@@ -187,7 +180,6 @@ __device__ __forceinline__ void collide_node(const MarchSmem& sm, const D2Args<f
         const float jy = (jy_of(f[0]) + 0.5f * Fy0) + (jy_of(f[1]) + 0.5f * Fy1);
         ux = jx * inv_rt;
         uy = jy * inv_rt;
-        const int n = y * a.pitch + x;
         if (a.macro) {
             a.macro[n] = rho0;
             a.macro[a.plane + n] = rho1;
@@ -213,6 +205,10 @@ __device__ __forceinline__ void collide_node(const MarchSmem& sm, const D2Args<f
 // leaves after a second bounded wait for its copies in flight.
 constexpr long long kCopyWaitLimit = 1000000000LL;
 
+// Bulk copies of a run, in issue order: copy 0 holds the sources of the two
+// halo rows below the run (rows ys - 2, ys - 1), copy j + 1 those of block j
+// (rows ys + 8j ... ys + 8j + 7; block K, past the run, only its first two
+// rows, the halo above).  Copy m goes to buffer m % MNB.
 __global__ void __launch_bounds__(MTX * MRB, 2)
     d2q9_march_kernel(const __grid_constant__ D2Args<float, float> a, const __grid_constant__ CUtensorMap tmap,
                       const int4* __restrict__ runs, const uint8_t* __restrict__ run_flags) {
@@ -225,78 +221,83 @@ __global__ void __launch_bounds__(MTX * MRB, 2)
     const int ys = (run.x >> 16) * MRB - a.yoff;
     const int K = run.y;
     const int xs = (x0 - 3) & ~3;  // x0 >= 3 for interior tiles: a 16-byte aligned box start
-    // thread 0 alone issues copies and counts, per buffer, the copies issued
-    // and the ones waited for (it waits for completions on behalf of the CTA)
-    int issued[2] = {0, 0}, waited[2] = {0, 0};
-    // self-check before any copy: both destinations 128-byte aligned, else
+    // self-check before any copy: every destination 128-byte aligned, else
     // mark the status word and leave without issuing anything
-    if (((smem_u32(&sm.box[0]) | smem_u32(&sm.box[1])) & 127u) != 0u) {
+    unsigned mis = 0u;
+#pragma unroll
+    for (int q = 0; q < MNB; ++q) mis |= smem_u32(&sm.box[q]) & 127u;
+    if (mis) {
         if (threadIdx.x == 0) atomicOr(a.status, 4u);
         return;
     }
-    if (threadIdx.x == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // the prologue's sources into buffer 1, the first block's into buffer 0
-        issue_box(sm, &tmap, 1, xs, ys - 3);
-        issued[1] += 1;
-        issue_box(sm, &tmap, 0, xs, ys + 1);
-        issued[0] += 1;
-    }
-    __syncthreads();
-    // wait for the oldest copy not yet waited for in buffer b; on a timeout
-    // the status word is marked, the copies still in flight get a second
-    // bounded wait, and every thread leaves together
-    auto wait_box = [&](int b) -> bool {
+    // thread 0 alone issues the copies and waits for them on behalf of the CTA
+    int issued = 0, waited = 0;
+    auto issue = [&](int m) {  // copy m: the sources of rows [first pulled row - 1, + MBH)
+        const int row0 = m == 0 ? ys - 3 : ys + MRB * (m - 1) - 1;
+        const int b = m % MNB;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the buffer first
+        mbar_expect_tx(&sm.bar[b], MBOX_BYTES);
+        tma_load_box(&sm.box[b].v[0][0][0], &tmap, xs, row0, &sm.bar[b]);
+        issued = m + 1;
+    };
+    auto wait_copy = [&](int m) -> bool {  // copies complete in issue order per buffer: use m / MNB of buffer m % MNB
         if (threadIdx.x == 0) {
-            int ok = mbar_wait(&sm.bar[b], (unsigned)(waited[b] & 1), kCopyWaitLimit) ? 1 : 0;
-            waited[b] += 1;
+            int ok = mbar_wait(&sm.bar[m % MNB], (unsigned)((m / MNB) & 1), kCopyWaitLimit) ? 1 : 0;
+            waited = m + 1;
             if (!ok) {
                 atomicOr(a.status, 2u);
-                for (int q = 0; q < 2; ++q)
-                    if (issued[q] > waited[q] - (q == b ? 1 : 0))
-                        mbar_wait(&sm.bar[q], (unsigned)((issued[q] - 1) & 1), kCopyWaitLimit);
+                for (int q = m; q < issued; ++q)  // copies still in flight end before the CTA does
+                    mbar_wait(&sm.bar[q % MNB], (unsigned)((q / MNB) & 1), kCopyWaitLimit);
             }
             sm.ok = ok;
         }
         __syncthreads();
         return sm.ok != 0;
     };
-    // prologue: rows ys - 2 ... ys + 1 from sources [ys - 3, ys + 7); the
-    // pulls of rows ys, ys + 1 are kept for the first block
-    if (!wait_box(1)) return;
-    density_rows(sm, a, 1, ys - 3, xs, x0, ys, ys - 2, 4, 3, sm.fsave[1], 2);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < MNB; ++q) mbar_init(&sm.bar[q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        issue(0);
+        issue(1);
+        if (K >= 1) issue(2);
+    }
     __syncthreads();
-    for (int k = 0; k < K; ++k) {
-        const int Y = ys + k * MRB;
-        const int b = k & 1;
-        // next block's sources into the other buffer (free since the barrier that ended the last block)
-        if (threadIdx.x == 0 && k + 1 < K) {
-            issue_box(sm, &tmap, b ^ 1, xs, Y + MRB + 1);
-            issued[b ^ 1] += 1;
-        }
-        if (!wait_box(b)) return;
-        // densities of rows Y + 2 ... Y + 9; the last two rows' pulls are kept for the next block
-        density_rows(sm, a, b, Y + 1, xs, x0, ys, Y + 2, MRB, 0, sm.fsave[b], MRB - 2);
-        __syncthreads();
-        // rows Y ... Y + 7: pulled again from the box (rows Y + 2 on), or saved by the last block
-        {
-            const int y = Y + w;
-            const int x = x0 + lane;
-            const unsigned info = __ldg(a.info + y * a.pitch + x);
-            float f[2][9];
-            if (w >= 2) {
-                pull_box(sm, b, Y + 1, xs, x, y, info, f);
-            } else {
-#pragma unroll
-                for (int k2 = 0; k2 < 2; ++k2)
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) f[k2][i] = sm.fsave[b ^ 1][k2 * 9 + i][w][lane];
-            }
-            collide_node(sm, a, x0, ys, y, info, (run_flags[run.z + k] & BLOCK_SOLID) != 0, f);
+    (void)waited;
+    // halo rows below the run (warps 0, 1), their halo columns (warp 2)
+    if (!wait_copy(0)) return;
+    if (w < 2) {
+        float f[2][9];
+        density_node(sm, a, 0, ys - 3, xs, ys, x0 + lane, ys - 2 + w, lane + 2, f);
+    }
+    halo_columns(sm, a, 0, ys - 3, xs, x0, ys, ys - 2, 2, 2);
+    __syncthreads();  // buffer 0 is free again
+    // block j: pull rows ys + 8j + w (densities now, collision at block j + 1,
+    // once the window holds the two rows above them); collide block j - 1
+    float fa[2][9], fb[2][9];
+    auto block = [&](int j, float (&fnew)[2][9], float (&fold)[2][9]) -> bool {
+        if (threadIdx.x == 0 && j + 2 <= K) issue(j + 3);  // buffer (j + 3) % 3 last served copy j
+        if (!wait_copy(j + 1)) return false;
+        const int b = (j + 1) % MNB;
+        const int row0 = ys + MRB * j - 1;
+        const int Y = ys + MRB * j;
+        if (j < K) {
+            density_node(sm, a, b, row0, xs, ys, x0 + lane, Y + w, lane + 2, fnew);
+            halo_columns(sm, a, b, row0, xs, x0, ys, Y, MRB, j & (MRB - 1));
+        } else {
+            if (w < 2) density_node(sm, a, b, row0, xs, ys, x0 + lane, Y + w, lane + 2, fnew);
+            halo_columns(sm, a, b, row0, xs, x0, ys, Y, 2, 2);
         }
         __syncthreads();
+        if (j >= 1) {
+            const int y = Y - MRB + w;
+            collide_node(sm, a, x0, ys, y, (run_flags[run.z + j - 1] & BLOCK_SOLID) != 0, fold);
+        }
+        __syncthreads();  // window rows and the box buffer are free for the next block
+        return true;
+    };
+    for (int j = 0; j <= K; j += 2) {
+        if (!block(j, fa, fb)) return;
+        if (j + 1 <= K && !block(j + 1, fb, fa)) return;
     }
 }
 

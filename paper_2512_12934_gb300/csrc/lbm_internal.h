@@ -87,6 +87,10 @@ struct D2Args {
     // outlet node saved for d2q9_outlet_chi_kernel (OC_STRIDE values); NULL
     // for the lagged chi
     R* __restrict__ oc_save;
+    // moving walls beyond the closed edges y = 0 (index 0) and y = ny - 1
+    // (index 1): x-velocity; wall_on = 0 when both are at rest
+    int wall_on;
+    R wall_ux[2];
     R G12;
     R Gw[2];
     R s[2][9];

@@ -113,6 +113,8 @@ def load():
     L.lbm_tile_stats.argtypes = [c_ctx] + [ctypes.POINTER(ctypes.c_int)] * 3 + [ctypes.POINTER(ctypes.c_int64)] * 2
     L.lbm_set_graph_mode.restype = ctypes.c_int
     L.lbm_set_graph_mode.argtypes = [c_ctx, ctypes.c_int]
+    L.lbm_set_wall_velocity.restype = ctypes.c_int
+    L.lbm_set_wall_velocity.argtypes = [c_ctx, ctypes.c_int, ctypes.c_double]
     L.lbm_set_chi_timing.restype = ctypes.c_int
     L.lbm_set_chi_timing.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_set_schedule.restype = ctypes.c_int
@@ -258,6 +260,11 @@ class Solver:
         _check(st, None)
         self.h = h
         self.precision = precision
+        wu = cfg.get("wall_ux")
+        if wu is not None and not three:
+            for side, v in zip(("ymin", "ymax"), wu):
+                if v:
+                    self.set_wall_velocity(side, v)
 
     def close(self):
         if getattr(self, "h", None):
@@ -349,6 +356,10 @@ class Solver:
     def set_schedule(self, name):
         """'graphs' (default) or 'persistent' (lbm_set_schedule)."""
         _check(load().lbm_set_schedule(self.h, SCHEDULES[name]), self.h)
+
+    def set_wall_velocity(self, side, ux):
+        """Moving wall beyond the closed edge 'ymin' or 'ymax' (lbm_set_wall_velocity)."""
+        _check(load().lbm_set_wall_velocity(self.h, SIDES[side], float(ux)), self.h)
 
     def set_chi_timing(self, same_step):
         """chi from the step's own fluxes (True) or the previous step's

@@ -219,6 +219,22 @@ def tjunction(Wc=40, length_factor=20, Wd=None, side_len=None, x_side=None, Ca=0
                     {"Wc": Wc, "Wd": Wd, "x_side": x_side, "Ca": Ca, "q_ratio": q_ratio, "M": M})
 
 
+def sheared_droplet(nx=200, ny=100, R=20.0, U=0.01, G12=1.4, M=1.0, nu_m=1.0 / 6, seed=2512008,
+                    width=4.0) -> Workload:
+    """Taylor deformation (Sec. III A, Fig. 4): a droplet (component 1,
+    viscosity M nu_m) centred between walls beyond the closed y edges that
+    move along x at -U (bottom) and +U (top), periodic in x; matrix
+    component 2 with viscosity nu_m.  The walls sit halfway beyond rows 0
+    and ny - 1, a distance ny apart, so the imposed shear rate is 2U / ny."""
+    cfg = _base_cfg(nx, ny, (1, 0), G12, (0.0, 0.0), (M * nu_m, nu_m))
+    cfg["wall_ux"] = (-float(U), float(U))
+    rho = droplet_fields(nx, ny, nx / 2 - 0.5, ny / 2 - 0.5, R, width=width)
+    u = np.zeros((2, ny, nx))
+    u[0] = (-U + 2.0 * U * (np.arange(ny) + 0.5) / ny)[:, None]
+    return Workload("sheared_droplet_%dx%d" % (nx, ny), cfg, None, rho, u, 0,
+                    {"R": R, "U": U, "M": M, "shear_rate": 2.0 * U / ny})
+
+
 def tjunction_ensemble(n=256, seed=2512004, wc_range=(40, 120), G12=2.0, Gw=(0.2, -0.2), gamma=0.25,
                        u_cap=0.05, length_factor=20):
     """Seeded ensemble of T-junction droplet generators with uneven sizes and
