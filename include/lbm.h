@@ -255,6 +255,20 @@ lbm_status lbm_set_graph_mode(lbm_ctx* ctx, int use_graphs);
  * (a running batch picks it up when rebuilt).  Waits for the stream. */
 lbm_status lbm_set_wall_velocity(lbm_ctx* ctx, int side, double ux);
 
+/* Wettability, Eq. 12.  The paper makes the adhesion coefficient of Eq. 11
+ * depend on a phase quantity rho^e through a threshold delta and two
+ * functions g1, g2 that it does not define (they come from its ref. [42]).
+ * delta in (0, 1] switches on this library's reading: one coefficient for
+ * both components, G_w(rho^e) with rho^e = (rho_1 - rho_2)/(rho_1 + rho_2)
+ * at the node: Gw[0] (lbm_params) where rho^e > delta, Gw[1] where
+ * rho^e < -delta, and the linear pieces g1 = Gw[0] rho^e/delta on
+ * (0, delta], g2 = -Gw[1] rho^e/delta on (-delta, 0] between them (zero
+ * on the interface itself).  In either pure phase the dominant component
+ * then feels exactly its constant coefficient; only the contact-line region
+ * changes.  delta <= 0 (the default): each component keeps its constant
+ * Gw[k].  Applies from the next step.  Waits for the context's stream. */
+lbm_status lbm_set_wetting(lbm_ctx* ctx, double delta);
+
 /* Timing of chi, the outlet mass-flux correction (Eqs. 22, 23).
  *  same_step = 0 (default): chi of a step comes from the previous step's
  *    inlet and outlet fluxes (one-step lag), so each step needs no grid-wide

@@ -207,6 +207,8 @@ typedef struct {
     double s_full[2][NQ];
     int chi_same_step; /* 1: chi of Eq. 23 from this step's fields (t + dt, as printed); 0: lagged */
     double wall_ux[2];  /* x-velocity of the walls beyond the closed edges y = 0 and y = ny-1 */
+    int wet_interp;     /* 1: Eq. 12's phase-dependent adhesion coefficient (reading below) */
+    double wet_delta;   /* its delta */
 } orc_params;
 
 typedef struct {
@@ -281,6 +283,21 @@ static int face_on_side(const orc_state* st, int side) {
     for (int f = 0; f < st->nfaces; ++f)
         if (st->face[f].side == side) return 1;
     return 0;
+}
+
+/* Eq. 12: the adhesion coefficient of both components at a node whose phase
+ * indicator is rho_e = (rho_1 - rho_2)/(rho_1 + rho_2): G_w,1 beyond delta
+ * (fluid 1), G_w,2 below -delta (fluid 2), and between them the two linear
+ * pieces g1 = G_w,1 rho_e/delta on (0, delta] and g2 = -G_w,2 rho_e/delta on
+ * (-delta, 0], which meet at 0 on the interface.  Without wet_interp each
+ * component keeps its own constant G_w,k. */
+static double adhesion_coeff(const orc_state* st, int k, double r1, double r2) {
+    if (!st->p.wet_interp) return st->p.Gw[k];
+    const double re = (r1 - r2) / (r1 + r2), d = st->p.wet_delta;
+    if (re > d) return st->p.Gw[0];
+    if (re > 0.0) return st->p.Gw[0] * re / d;
+    if (re > -d) return -st->p.Gw[1] * re / d;
+    return st->p.Gw[1];
 }
 
 /* Virtual site for the psi / solid-indicator stencil (Eqs. 10, 11, 24, 25).
@@ -653,9 +670,10 @@ static void one_step(orc_state* st) {
             for (int k = 0; k < NCOMP; ++k) {
                 int kb = 1 - k; /* the other component */
                 double psik = rho[(size_t)k * N + n];
-                double Fx = -st->p.G12 * psik * gx[kb] - st->p.Gw[k] * psik * ax +
+                const double gw = adhesion_coeff(st, k, rho[n], rho[N + n]);
+                double Fx = -st->p.G12 * psik * gx[kb] - gw * psik * ax +
                             st->p.body[0] * psik / rt;
-                double Fy = -st->p.G12 * psik * gy[kb] - st->p.Gw[k] * psik * ay +
+                double Fy = -st->p.G12 * psik * gy[kb] - gw * psik * ay +
                             st->p.body[1] * psik / rt;
                 F[((size_t)k * 2 + 0) * N + n] = Fx;
                 F[((size_t)k * 2 + 1) * N + n] = Fy;
@@ -816,8 +834,9 @@ void orc_eval_forces(const orc_state* st, const double* psi, double* F) {
                 }
             for (int k = 0; k < 2; ++k) {
                 double pk = st->solid[n] ? 0.0 : psi[(size_t)k * N + n];
-                F[((size_t)k * 2 + 0) * N + n] = -st->p.G12 * pk * gx[1 - k] - st->p.Gw[k] * pk * ax;
-                F[((size_t)k * 2 + 1) * N + n] = -st->p.G12 * pk * gy[1 - k] - st->p.Gw[k] * pk * ay;
+                const double gw = st->solid[n] ? 0.0 : adhesion_coeff(st, k, psi[n], psi[N + n]);
+                F[((size_t)k * 2 + 0) * N + n] = -st->p.G12 * pk * gx[1 - k] - gw * pk * ax;
+                F[((size_t)k * 2 + 1) * N + n] = -st->p.G12 * pk * gy[1 - k] - gw * pk * ay;
             }
         }
 }

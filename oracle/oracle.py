@@ -25,7 +25,12 @@ Readings taken where the paper is silent, garbled or inconsistent:
     ("adjusted based on the phase with the highest viscosity", Sec. III A);
     the unadjusted scheme uses each component's own s_nu,k.
  5. Eq. 12 (G_w interpolation) depends on quantities the paper does not
-    define; G_w,k is a constant per component.
+    define (rho^e, delta, g1, g2).  By default G_w,k is a constant per
+    component.  With cfg["wetting_delta"] = delta > 0 one coefficient
+    G_w(rho^e) acts on both components, rho^e = (rho_1 - rho_2)/(rho_1 +
+    rho_2): G_w,1 for rho^e > delta, G_w,2 for rho^e < -delta, and the
+    linear pieces G_w,1 rho^e/delta on (0, delta], -G_w,2 rho^e/delta on
+    (-delta, 0] between them (zero on the interface itself).
  6. psi = 0 on solid nodes; wettability enters only through Eq. 11.
     Outside a closed (non-periodic, non-open) edge the lattice is solid.
  7. Eq. 10 is used with the printed weights as is (their second moment
@@ -77,7 +82,7 @@ class _Params(ctypes.Structure):
         ("s_e", ctypes.c_double), ("s_q", ctypes.c_double), ("s_eps_mode", ctypes.c_int),
         ("body", ctypes.c_double * 2), ("use_s_full", ctypes.c_int),
         ("s_full", (ctypes.c_double * 9) * 2), ("chi_same_step", ctypes.c_int),
-        ("wall_ux", ctypes.c_double * 2),
+        ("wall_ux", ctypes.c_double * 2), ("wet_interp", ctypes.c_int), ("wet_delta", ctypes.c_double),
     ]
 
 
@@ -201,6 +206,9 @@ class Oracle2D:
         body = cfg.get("body", (0.0, 0.0))
         p.body[0], p.body[1] = body[0], body[1]
         p.chi_same_step = int(cfg.get("chi_same_step", 0))
+        wet = cfg.get("wetting_delta")
+        p.wet_interp = 1 if wet else 0
+        p.wet_delta = float(wet) if wet else 1.0
         wu = cfg.get("wall_ux", (0.0, 0.0))
         p.wall_ux[0], p.wall_ux[1] = float(wu[0]), float(wu[1])
         sf = cfg.get("s_full")

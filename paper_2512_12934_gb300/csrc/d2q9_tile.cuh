@@ -139,21 +139,11 @@ __device__ __forceinline__ R feq_(int i, R rho, R ux, R uy) {
 // f*_i(x - e_i); a set bit i in `info` means that source is solid or outside
 // a closed edge, and halfway bounce-back (Eq. B1) takes f*_opp(i)(x).
 
-// Interior pull: every source lies inside the grid, no wrap needed.  Nodes
-// without a solid neighbour (no bounce-back bit, the common case) take the
-// sources straight from their offsets.
+// Interior pull: every source lies inside the grid, no wrap needed.
 template <typename S, typename R>
 __device__ __forceinline__ void pull_interior(const D2Args<S, R>& a, int n, unsigned info, R (&f)[2][9]) {
     R ref[2];
     node_ref(a, n, ref);
-    if ((info & 0x1ffu) == 0u) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-                f[k][i] = Pop<S, R>::ld(a.fin, (k * 9 + i) * a.plane + n - ex_(i) - ey_(i) * a.pitch, w_<R>(i) * ref[k]);
-        return;
-    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const bool bb = (info >> i) & 1u;
@@ -1114,6 +1104,23 @@ __device__ __forceinline__ void psi_gradient(RR rr, R& g0x, R& g0y, R& g1x, R& g
     }
 }
 
+// Adhesion coefficients of Eq. 11 for the two components at a node with
+// densities rho0, rho1.  Eq. 12 (wet_interp): one coefficient for both,
+// G_w,1 where rho^e = (rho0 - rho1)/(rho0 + rho1) > delta, G_w,2 where
+// rho^e < -delta, and the linear pieces G_w,1 rho^e/delta on (0, delta],
+// -G_w,2 rho^e/delta on (-delta, 0] between them.
+template <typename S, typename R>
+__device__ __forceinline__ void adhesion_coeffs(const D2Args<S, R>& a, R rho0, R rho1, R& gw0, R& gw1) {
+    gw0 = a.Gw[0];
+    gw1 = a.Gw[1];
+    if (a.wet_interp) {
+        const R re = (rho0 - rho1) / (rho0 + rho1), d = a.wet_delta;
+        const R g = re > d ? a.Gw[0] : (re > R(0) ? a.Gw[0] * re / d : (re > -d ? -a.Gw[1] * re / d : a.Gw[1]));
+        gw0 = g;
+        gw1 = g;
+    }
+}
+
 // Eq. 11's sum sum_e w(|e|^2) e s(x + e), with sol(dy, dx) the solid
 // indicator (1 solid, 0 fluid) at offset (dx, dy).
 template <typename R, typename SOL>
@@ -1215,10 +1222,12 @@ __device__ __forceinline__ void step_tile(const D2Args<S, R>& a, int bxy, unsign
             adhesion_sum<R>([&](int dy, int dx) { return sm.sol[ty + 2 + dy][tx + 2 + dx]; }, ax, ay);
         const R rt = rho0 + rho1;
         const R inv_rt = R(1) / rt;
-        Fx0 = -a.G12 * rho0 * g1x - a.Gw[0] * rho0 * ax + a.body[0] * rho0 * inv_rt;
-        Fy0 = -a.G12 * rho0 * g1y - a.Gw[0] * rho0 * ay + a.body[1] * rho0 * inv_rt;
-        Fx1 = -a.G12 * rho1 * g0x - a.Gw[1] * rho1 * ax + a.body[0] * rho1 * inv_rt;
-        Fy1 = -a.G12 * rho1 * g0y - a.Gw[1] * rho1 * ay + a.body[1] * rho1 * inv_rt;
+        R gw0, gw1;
+        adhesion_coeffs(a, rho0, rho1, gw0, gw1);
+        Fx0 = -a.G12 * rho0 * g1x - gw0 * rho0 * ax + a.body[0] * rho0 * inv_rt;
+        Fy0 = -a.G12 * rho0 * g1y - gw0 * rho0 * ay + a.body[1] * rho0 * inv_rt;
+        Fx1 = -a.G12 * rho1 * g0x - gw1 * rho1 * ax + a.body[0] * rho1 * inv_rt;
+        Fy1 = -a.G12 * rho1 * g0y - gw1 * rho1 * ay + a.body[1] * rho1 * inv_rt;
         // ---- Eqs. 7, 8: common velocity ----
         const R jx = (jx_of(f[0]) + R(0.5) * Fx0) + (jx_of(f[1]) + R(0.5) * Fx1);
         const R jy = (jy_of(f[0]) + R(0.5) * Fy0) + (jy_of(f[1]) + R(0.5) * Fy1);

@@ -115,6 +115,7 @@ struct lbm_ctx {
     void* oc_state = nullptr;
     // moving walls beyond the closed edges y = 0 / y = ny - 1 (x-velocity)
     double wall_ux[2] = {0.0, 0.0};
+    double wet_delta = 0.0;  // > 0: Eq. 12's phase-dependent adhesion coefficient
     // persistent schedule of a single context: a batch of one member
     int schedule = LBM_SCHEDULE_GRAPHS;
     lbm_batch* solo = nullptr;
@@ -212,6 +213,8 @@ D2Args<S, R> make_args_par(lbm_ctx* c, int in, bool write_macros) {
     a.wall_on = (c->wall_ux[0] != 0.0 || c->wall_ux[1] != 0.0) ? 1 : 0;
     a.wall_ux[0] = (R)c->wall_ux[0];
     a.wall_ux[1] = (R)c->wall_ux[1];
+    a.wet_interp = c->wet_delta > 0.0 ? 1 : 0;
+    a.wet_delta = (R)(c->wet_delta > 0.0 ? c->wet_delta : 1.0);
     a.G12 = (R)c->params.G12;
     a.Gw[0] = (R)c->params.Gw[0];
     a.Gw[1] = (R)c->params.Gw[1];
@@ -1657,6 +1660,20 @@ lbm_status lbm_set_wall_velocity(lbm_ctx* c, int side, double ux) {
         return fail(c, LBM_ERR_UNSUPPORTED, "moving walls are built for FP32 and FP64 storage");
     CK(cudaStreamSynchronize(c->stream));
     c->wall_ux[side == LBM_YMIN ? 0 : 1] = ux;
+    for (int p = 0; p < 2; ++p)  // captured steps carry the old arguments
+        if (c->gexec[p]) {
+            cudaGraphExecDestroy(c->gexec[p]);
+            c->gexec[p] = nullptr;
+        }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wetting(lbm_ctx* c, double delta) {
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
+    if (!std::isfinite(delta) || delta > 1.0) return fail(c, LBM_ERR_INVALID_ARG, "delta must be in (0, 1], or <= 0 to switch off");
+    CK(cudaStreamSynchronize(c->stream));
+    c->wet_delta = delta > 0.0 ? delta : 0.0;
     for (int p = 0; p < 2; ++p)  // captured steps carry the old arguments
         if (c->gexec[p]) {
             cudaGraphExecDestroy(c->gexec[p]);

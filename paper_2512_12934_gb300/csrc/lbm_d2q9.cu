@@ -18,9 +18,16 @@
 namespace lbm {
 namespace {
 
+// Fast tiles in FP32 fit in 64 registers; holding them there keeps four
+// 256-thread CTAs (eight of 128) resident per SM.
+template <typename R, int TX, int TY>
+__host__ __device__ constexpr int fast_min_blocks() {
+    return sizeof(R) == 4 ? 65536 / (TX * TY * 64) : 1;
+}
+
 // Single-instance step: one tile of the launch's list per CTA.
 template <typename S, typename R, int TX, int TY, bool GEN>
-__global__ void __launch_bounds__(TX * TY) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
+__global__ void __launch_bounds__(TX * TY, (fast_min_blocks<R, TX, TY>())) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
     static_assert(!GEN, "general tiles run d2q9_general_kernel");
     const int li = a.list_off + blockIdx.x;
     step_tile<S, R, TX, TY, false>(a, a.blocks[li], a.block_flags[li], 0u, -1);
@@ -54,7 +61,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<S, R>& b) {
 }
 
 template <typename S, typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) d2q9_batch_kernel(const __grid_constant__ BatchArgs<S, R> b) {
+__global__ void __launch_bounds__(TX * TY, (fast_min_blocks<R, TX, TY>())) d2q9_batch_kernel(const __grid_constant__ BatchArgs<S, R> b) {
     batch_tile<S, R, TX, TY, false>(b);
 }
 

@@ -172,10 +172,12 @@ __device__ __forceinline__ void collide_node(const MarchSmem& sm, const D2Args<f
             adhesion_sum<float>([&](int dy, int dx) { return sm.sol[wrow[dy + 2]][lane + 2 + dx]; }, ax, ay);
         const float rt = rho0 + rho1;
         const float inv_rt = 1.f / rt;
-        const float Fx0 = -a.G12 * rho0 * g1x - a.Gw[0] * rho0 * ax + a.body[0] * rho0 * inv_rt;
-        const float Fy0 = -a.G12 * rho0 * g1y - a.Gw[0] * rho0 * ay + a.body[1] * rho0 * inv_rt;
-        const float Fx1 = -a.G12 * rho1 * g0x - a.Gw[1] * rho1 * ax + a.body[0] * rho1 * inv_rt;
-        const float Fy1 = -a.G12 * rho1 * g0y - a.Gw[1] * rho1 * ay + a.body[1] * rho1 * inv_rt;
+        float gw0, gw1;
+        adhesion_coeffs(a, rho0, rho1, gw0, gw1);
+        const float Fx0 = -a.G12 * rho0 * g1x - gw0 * rho0 * ax + a.body[0] * rho0 * inv_rt;
+        const float Fy0 = -a.G12 * rho0 * g1y - gw0 * rho0 * ay + a.body[1] * rho0 * inv_rt;
+        const float Fx1 = -a.G12 * rho1 * g0x - gw1 * rho1 * ax + a.body[0] * rho1 * inv_rt;
+        const float Fy1 = -a.G12 * rho1 * g0y - gw1 * rho1 * ay + a.body[1] * rho1 * inv_rt;
         const float jx = (jx_of(f[0]) + 0.5f * Fx0) + (jx_of(f[1]) + 0.5f * Fx1);
         const float jy = (jy_of(f[0]) + 0.5f * Fy0) + (jy_of(f[1]) + 0.5f * Fy1);
         ux = jx * inv_rt;

@@ -91,6 +91,11 @@ struct D2Args {
     // (index 1): x-velocity; wall_on = 0 when both are at rest
     int wall_on;
     R wall_ux[2];
+    // Eq. 12: wet_interp = 1 gives both components one adhesion coefficient
+    // G_w(rho^e), rho^e = (rho_1 - rho_2)/(rho_1 + rho_2) (piecewise linear
+    // within wet_delta of the interface); 0: constant Gw[k] per component
+    int wet_interp;
+    R wet_delta;
     R G12;
     R Gw[2];
     R s[2][9];

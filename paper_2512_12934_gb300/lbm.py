@@ -115,6 +115,8 @@ def load():
     L.lbm_set_graph_mode.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_set_wall_velocity.restype = ctypes.c_int
     L.lbm_set_wall_velocity.argtypes = [c_ctx, ctypes.c_int, ctypes.c_double]
+    L.lbm_set_wetting.restype = ctypes.c_int
+    L.lbm_set_wetting.argtypes = [c_ctx, ctypes.c_double]
     L.lbm_set_chi_timing.restype = ctypes.c_int
     L.lbm_set_chi_timing.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_set_schedule.restype = ctypes.c_int
@@ -260,6 +262,8 @@ class Solver:
         _check(st, None)
         self.h = h
         self.precision = precision
+        if cfg.get("wetting_delta") and not three:
+            self.set_wetting(cfg["wetting_delta"])
         wu = cfg.get("wall_ux")
         if wu is not None and not three:
             for side, v in zip(("ymin", "ymax"), wu):
@@ -360,6 +364,11 @@ class Solver:
     def set_wall_velocity(self, side, ux):
         """Moving wall beyond the closed edge 'ymin' or 'ymax' (lbm_set_wall_velocity)."""
         _check(load().lbm_set_wall_velocity(self.h, SIDES[side], float(ux)), self.h)
+
+    def set_wetting(self, delta):
+        """Eq. 12's phase-dependent adhesion coefficient (lbm_set_wetting);
+        delta <= 0 switches it off."""
+        _check(load().lbm_set_wetting(self.h, float(delta)), self.h)
 
     def set_chi_timing(self, same_step):
         """chi from the step's own fluxes (True) or the previous step's

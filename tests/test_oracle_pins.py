@@ -755,3 +755,67 @@ def test_moving_wall_gives_exact_plane_couette_flow():
     # wrong sign or a wall speed dropped would break the profile: check the
     # shear stress sign too (momentum flows from the moving wall inwards)
     assert np.all(np.diff(u[0][:, 0]) > 0)
+
+
+def _wall_box(delta, Gw=(0.4, -0.25)):
+    nx, ny = 12, 10
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[0] = solid[-1] = 1
+    cfg = W._base_cfg(nx, ny, (1, 0), 0.0, Gw, (0.1, 0.1))
+    if delta:
+        cfg["wetting_delta"] = delta
+    rho = np.full((2, ny, nx), 0.5)
+    rho[:, solid != 0] = 0
+    return O.Oracle2D(cfg, solid, rho), solid
+
+
+def test_eq12_wetting_reading_reduces_to_constant_coefficients_in_pure_phases():
+    """Eq. 12 as read: one coefficient G_w(rho^e) for both components, equal
+    to G_w,1 where rho^e > delta and G_w,2 where rho^e < -delta.  In fluid 1
+    (and in fluid 2) the dominant component feels exactly the constant
+    per-component adhesion of Eq. 11."""
+    o_int, solid = _wall_box(0.5)
+    o_cst, _ = _wall_box(None)
+    ny, nx = solid.shape
+    for major in (0, 1):
+        psi = np.full((2, ny, nx), 0.001)
+        psi[major] = 1.0
+        psi[:, solid != 0] = 0
+        Fi, Fc = o_int.eval_forces(psi), o_cst.eval_forces(psi)
+        assert np.max(np.abs(Fi[major] - Fc[major])) < 1e-16
+        assert np.max(np.abs(Fc[major])) > 1e-3             # the walls do push
+
+
+def test_eq12_wetting_reading_vanishes_on_the_interface_and_is_linear_within_delta():
+    delta = 0.5
+    o, solid = _wall_box(delta)
+    ny, nx = solid.shape
+    sol = (solid != 0)
+    fluid = ~sol
+    # adhesion direction field (G12 = 0): F_k = -G_w psi_k A with A = sum w s e
+    psi = np.zeros((2, ny, nx))
+    psi[:, fluid] = 0.5                                   # rho^e = 0 everywhere
+    F = o.eval_forces(psi)
+    assert np.max(np.abs(F)) < 1e-16
+    Gw1, Gw2 = 0.4, -0.25
+    for re, want in ((0.25, Gw1 * 0.25 / delta), (-0.25, Gw2 * 0.25 / delta), (0.7, Gw1), (-0.7, Gw2)):
+        psi[0][fluid], psi[1][fluid] = (1 + re) / 2, (1 - re) / 2
+        F = o.eval_forces(psi)
+        ref, _ = _wall_box(None, Gw=(1.0, 1.0))            # constant coefficient 1: -psi_k A
+        A = ref.eval_forces(psi)
+        ratio = F[0][1][1, :] / A[0][1][1, :]              # row next to the bottom wall, y-force
+        assert np.allclose(ratio, want, rtol=1e-14, atol=0)
+
+
+def test_eq12_wetting_reading_is_symmetric_under_label_swap():
+    """Swapping the component labels and G_w,1 with G_w,2 swaps the forces."""
+    delta = 0.5
+    a, solid = _wall_box(delta, Gw=(0.4, -0.25))
+    b, _ = _wall_box(delta, Gw=(-0.25, 0.4))
+    ny, nx = solid.shape
+    rng = np.random.default_rng(12)
+    psi = rng.uniform(0.05, 1.0, (2, ny, nx))
+    psi[:, solid != 0] = 0
+    Fa = a.eval_forces(psi)
+    Fb = b.eval_forces(psi[::-1].copy())
+    assert np.max(np.abs(Fa - Fb[::-1])) < 1e-15
