@@ -58,7 +58,7 @@ enum { LBM_XMIN = 0, LBM_XMAX = 1, LBM_YMIN = 2, LBM_YMAX = 3, LBM_ZMIN = 4, LBM
 enum { LBM_SEPS_OWN_NU = 0, LBM_SEPS_MAX_NU = 1 };
 
 /* Step schedules (lbm_set_schedule, lbm_batch_set_schedule). */
-enum { LBM_SCHEDULE_GRAPHS = 0, LBM_SCHEDULE_PERSISTENT = 1 };
+enum { LBM_SCHEDULE_GRAPHS = 0, LBM_SCHEDULE_PERSISTENT = 1, LBM_SCHEDULE_GRAPHS_EARLY = 2 };
 
 typedef struct lbm_ctx lbm_ctx; /* opaque, library-owned */
 
@@ -283,12 +283,20 @@ lbm_status lbm_set_wetting(lbm_ctx* ctx, double delta);
  * otherwise.  Waits for the context's stream. */
 lbm_status lbm_set_chi_timing(lbm_ctx* ctx, int same_step);
 
-/* Schedule of lbm_step for this context: LBM_SCHEDULE_GRAPHS (default) or
- * LBM_SCHEDULE_PERSISTENT (FP32 storage only; see lbm_batch_set_schedule,
- * of which this is the one-member case).  Under the persistent schedule
- * lbm_sync also reports LBM_ERR_TIMEOUT, and lbm_enable_kernel_timing takes
- * no samples.  Waits for the context's stream first. */
+/* Schedule of lbm_step for this context: LBM_SCHEDULE_GRAPHS (default),
+ * LBM_SCHEDULE_GRAPHS_EARLY or LBM_SCHEDULE_PERSISTENT (FP32 storage only);
+ * see lbm_batch_set_schedule, of which this is the one-member case.  Under
+ * the persistent schedule lbm_sync also reports LBM_ERR_TIMEOUT, and
+ * lbm_enable_kernel_timing takes no samples.  Waits for the context's
+ * stream first.  2D contexts only (LBM_ERR_UNSUPPORTED for D3Q19). */
 lbm_status lbm_set_schedule(lbm_ctx* ctx, int schedule);
+
+/* The context's schedule, and in *early_in_use whether its instantiated
+ * step graphs launch early (1) or, the driver having refused the
+ * programmatic edges, are plain graphs (0; also before the first graph is
+ * built, and always for D3Q19 contexts, which report LBM_SCHEDULE_GRAPHS).
+ * Never blocks. */
+lbm_status lbm_get_schedule(lbm_ctx* ctx, int* schedule, int* early_in_use);
 
 /* FP64 mass of each component of caller-owned D2Q9 populations, for callers
  * that cannot allocate device memory (a process whose device memory is all
@@ -375,8 +383,23 @@ lbm_status lbm_batch_set_graph_mode(lbm_batch* b, int use_graphs);
  *    tile's node threads.  Results equal the graph schedule's to the FP32
  *    parity tolerance (not bit for bit: the general tiles' staging is
  *    compiled separately).
- * The schedule applies from the next lbm_batch_step. */
+ *  LBM_SCHEDULE_GRAPHS_EARLY: the graph schedule with early launches.  In
+ *    the captured graphs every dependency between two kernels becomes a
+ *    programmatic one that lets the later kernel launch as soon as all CTAs
+ *    of the earlier one have started; each step kernel waits on the device
+ *    (griddepcontrol.wait, its first instruction) until the grids it
+ *    depends on have completed and their writes are visible.  Every memory
+ *    access keeps the plain graph's order, so results are bit-identical to
+ *    LBM_SCHEDULE_GRAPHS; the launch latency between steps is hidden behind
+ *    the previous step.  If the driver refuses the programmatic edges, the
+ *    plain graphs are used (lbm_batch_get_schedule reports which).
+ * The schedule applies from the next lbm_batch_step; switching between the
+ * two graph forms waits for the batch's stream and drops its graphs. */
 lbm_status lbm_batch_set_schedule(lbm_batch* b, int schedule);
+
+/* The batch's schedule and whether its step graphs launch early (see
+ * lbm_get_schedule).  Never blocks. */
+lbm_status lbm_batch_get_schedule(lbm_batch* b, int* schedule, int* early_in_use);
 
 /* CTAs of the batch's last persistent launch (0 before the first). */
 lbm_status lbm_batch_persistent_grid(lbm_batch* b, int* ctas);

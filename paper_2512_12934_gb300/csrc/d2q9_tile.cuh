@@ -53,6 +53,14 @@ __device__ __forceinline__ T ld_mut(const T* p) {
 }
 
 
+// Early-launch graphs (programmatic dependent launch): a step's kernels may
+// be launched while the previous step's grids still run, as soon as all of
+// their CTAs have started.  Every kernel a step graph holds therefore waits
+// here, before it touches any buffer, until the grids it depends on have
+// completed and their memory is visible.  A kernel launched without such a
+// dependency returns from the wait at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---- D2Q9 lattice (velocity order fixed by Eqs. 13, 14, 20 and B2) -------
 __host__ __device__ constexpr int ex_(int i) {
     return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);

@@ -102,6 +102,7 @@ struct lbm_ctx {
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int gexec_early[2] = {0, 0};  // the graph of that parity launches its steps early
     // sampled per-launch timing
     std::vector<int> h_faceid, h_nbrid;  // per node (unpitched): face id + 1, inward-neighbour face id + 1
     std::vector<uint8_t> host_solid;   // pitched copy of the solid mask
@@ -143,6 +144,58 @@ lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
     } while (0)
 
 constexpr int kGraphSteps = 32;  // even: a replay leaves the ping-pong parity unchanged
+
+// Early-launch step graphs (LBM_SCHEDULE_GRAPHS_EARLY): every edge between
+// two kernel nodes of a captured step graph becomes a programmatic edge that
+// fires once all CTAs of the upstream kernel have started.  The downstream
+// kernel is then launched while the upstream one still runs, and its CTAs
+// wait on the device (griddepcontrol.wait at the top of every step kernel)
+// until the upstream grids have completed and their writes are visible:
+// the order of all memory accesses is that of the plain graph, only the
+// launch latency between steps is hidden.
+cudaError_t early_launch_edges(cudaGraph_t g) {
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &n);
+    if (e != cudaSuccess || n == 0) return e;
+    std::vector<cudaGraphNode_t> from(n), to(n);
+    std::vector<cudaGraphEdgeData> ed(n);
+    e = cudaGraphGetEdges(g, from.data(), to.data(), ed.data(), &n);
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+        cudaGraphNodeType tf, tt;
+        e = cudaGraphNodeGetType(from[i], &tf);
+        if (e == cudaSuccess) e = cudaGraphNodeGetType(to[i], &tt);
+        if (e != cudaSuccess) break;
+        if (tf != cudaGraphNodeTypeKernel || tt != cudaGraphNodeTypeKernel ||
+            ed[i].type != cudaGraphDependencyTypeDefault || ed[i].from_port != cudaGraphKernelNodePortDefault)
+            continue;
+        e = cudaGraphRemoveDependencies(g, &from[i], &to[i], &ed[i], 1);
+        cudaGraphEdgeData pe{};
+        pe.from_port = cudaGraphKernelNodePortLaunchCompletion;
+        pe.type = cudaGraphDependencyTypeProgrammatic;
+        if (e == cudaSuccess) e = cudaGraphAddDependencies(g, &from[i], &to[i], &pe, 1);
+    }
+    return e;
+}
+
+// Instantiate a captured step graph.  early: first the early-launch form;
+// if the driver refuses it, the plain graph (*early_used tells which).
+cudaError_t instantiate_step_graph(cudaGraph_t g, bool early, cudaGraphExec_t* out, int* early_used) {
+    *early_used = 0;
+    if (early) {
+        cudaGraph_t eg = nullptr;
+        cudaError_t e = cudaGraphClone(&eg, g);
+        if (e == cudaSuccess) e = early_launch_edges(eg);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(out, eg, 0);
+        if (eg) cudaGraphDestroy(eg);
+        if (e == cudaSuccess) {
+            *early_used = 1;
+            return e;
+        }
+        *out = nullptr;
+        cudaGetLastError();
+    }
+    return cudaGraphInstantiate(out, g, 0);
+}
 constexpr int kPersistSteps = 1024;  // steps per persistent launch
 // clock64 budget of one grid-barrier wait: ~1 s at the 2.07 GHz SM clock,
 // several hundred times the longest step of any batch measured
@@ -298,7 +351,8 @@ lbm_status ensure_graph(lbm_ctx* c, int par) {
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     c->cur = saved;
     if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[par], g, 0);
+    if (e == cudaSuccess)
+        e = instantiate_step_graph(g, c->schedule == LBM_SCHEDULE_GRAPHS_EARLY, &c->gexec[par], &c->gexec_early[par]);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         c->gexec[par] = nullptr;
@@ -957,6 +1011,7 @@ struct lbm_batch {
     cudaStream_t cap_stream = nullptr, side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int gexec_early[2] = {0, 0};
     int64_t launches = 0;
     // persistent schedule: one cooperative launch per run of up to
     // kPersistSteps steps, grid barriers with bounded waits between steps
@@ -1168,7 +1223,8 @@ lbm_status batch_graph(lbm_batch* b, int par) {
     cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
     b->bpar = saved;
     if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec[par], g, 0);
+    if (e == cudaSuccess)
+        e = instantiate_step_graph(g, b->schedule == LBM_SCHEDULE_GRAPHS_EARLY, &b->gexec[par], &b->gexec_early[par]);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         b->gexec[par] = nullptr;
@@ -1638,14 +1694,29 @@ lbm_status lbm_sync(lbm_ctx* c) {
 lbm_status lbm_set_schedule(lbm_ctx* c, int schedule) {
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
     if (c->d3) return fail(c, LBM_ERR_UNSUPPORTED, "not implemented for D3Q19 contexts");
-    if (schedule != LBM_SCHEDULE_GRAPHS && schedule != LBM_SCHEDULE_PERSISTENT)
+    if (schedule != LBM_SCHEDULE_GRAPHS && schedule != LBM_SCHEDULE_PERSISTENT &&
+        schedule != LBM_SCHEDULE_GRAPHS_EARLY)
         return fail(c, LBM_ERR_INVALID_ARG, "unknown schedule");
     if (schedule == LBM_SCHEDULE_PERSISTENT && c->precision != LBM_FP32)
         return fail(c, LBM_ERR_UNSUPPORTED, "the persistent schedule is built for FP32 storage only");
     if (schedule == LBM_SCHEDULE_PERSISTENT && c->chi_same_step)
         return fail(c, LBM_ERR_UNSUPPORTED, "the persistent schedule runs the lagged chi only");
     CK(cudaStreamSynchronize(c->stream));
+    if ((schedule == LBM_SCHEDULE_GRAPHS_EARLY) != (c->schedule == LBM_SCHEDULE_GRAPHS_EARLY))
+        for (int p = 0; p < 2; ++p)  // graphs of the other form
+            if (c->gexec[p]) {
+                cudaGraphExecDestroy(c->gexec[p]);
+                c->gexec[p] = nullptr;
+                c->gexec_early[p] = 0;
+            }
     c->schedule = schedule;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_schedule(lbm_ctx* c, int* schedule, int* early_in_use) {
+    if (!c || !schedule || !early_in_use) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    *schedule = c->d3 ? LBM_SCHEDULE_GRAPHS : c->schedule;
+    *early_in_use = c->d3 ? 0 : ((c->gexec[0] && c->gexec_early[0]) || (c->gexec[1] && c->gexec_early[1]));
     return LBM_OK;
 }
 
@@ -2051,11 +2122,28 @@ lbm_status lbm_batch_set_graph_mode(lbm_batch* b, int use_graphs) {
 
 lbm_status lbm_batch_set_schedule(lbm_batch* b, int schedule) {
     if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "batch is NULL");
-    if (schedule != LBM_SCHEDULE_GRAPHS && schedule != LBM_SCHEDULE_PERSISTENT)
+    if (schedule != LBM_SCHEDULE_GRAPHS && schedule != LBM_SCHEDULE_PERSISTENT &&
+        schedule != LBM_SCHEDULE_GRAPHS_EARLY)
         return bfail(b, LBM_ERR_INVALID_ARG, "unknown schedule");
     if (schedule == LBM_SCHEDULE_PERSISTENT && b->precision != LBM_FP32)
         return bfail(b, LBM_ERR_UNSUPPORTED, "the persistent schedule is built for FP32 storage only");
+    if ((schedule == LBM_SCHEDULE_GRAPHS_EARLY) != (b->schedule == LBM_SCHEDULE_GRAPHS_EARLY)) {
+        BCK(cudaStreamSynchronize(b->stream));
+        for (int p = 0; p < 2; ++p)
+            if (b->gexec[p]) {
+                cudaGraphExecDestroy(b->gexec[p]);
+                b->gexec[p] = nullptr;
+                b->gexec_early[p] = 0;
+            }
+    }
     b->schedule = schedule;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_schedule(lbm_batch* b, int* schedule, int* early_in_use) {
+    if (!b || !schedule || !early_in_use) return bfail(b, LBM_ERR_INVALID_ARG, "NULL argument");
+    *schedule = b->schedule;
+    *early_in_use = (b->gexec[0] && b->gexec_early[0]) || (b->gexec[1] && b->gexec_early[1]);
     return LBM_OK;
 }
 

@@ -29,12 +29,14 @@ __host__ __device__ constexpr int fast_min_blocks() {
 template <typename S, typename R, int TX, int TY, bool GEN>
 __global__ void __launch_bounds__(TX * TY, (fast_min_blocks<R, TX, TY>())) d2q9_step_kernel(const __grid_constant__ D2Args<S, R> a) {
     static_assert(!GEN, "general tiles run d2q9_general_kernel");
+    grid_dep_wait();
     const int li = a.list_off + blockIdx.x;
     step_tile<S, R, TX, TY, false>(a, a.blocks[li], a.block_flags[li], 0u, -1);
 }
 
 template <typename S, typename R, int TX, int TY, bool ROLES>
 __global__ void __maxnreg__((gen_maxreg<R, TX, TY, ROLES>())) d2q9_general_kernel(const __grid_constant__ D2Args<S, R> a) {
+    grid_dep_wait();
     const int li = a.list_off + blockIdx.x;
     step_tile<S, R, TX, TY, true, ROLES>(a, a.blocks[li], a.block_flags[li], a.block_strips[li], a.block_slot[li]);
 }
@@ -42,12 +44,10 @@ __global__ void __maxnreg__((gen_maxreg<R, TX, TY, ROLES>())) d2q9_general_kerne
 // Batched step: the list interleaves the tiles of many instances; each CTA
 // copies its instance's arguments into shared memory and runs the same tile
 // code, so a batch step equals stepping every member on its own.
-// Batched step: the list interleaves the tiles of many instances; each CTA
-// copies its instance's arguments into shared memory and runs the same tile
-// code, so a batch step equals stepping every member on its own.
 template <typename S, typename R, int TX, int TY, bool GEN, bool ROLES = true>
 __device__ __forceinline__ void batch_tile(const BatchArgs<S, R>& b) {
     __shared__ D2Args<S, R> sa;
+    grid_dep_wait();
     const int li = b.off + blockIdx.x;
     const int m = b.member[li];
     {
@@ -78,6 +78,7 @@ __global__ void __maxnreg__((gen_maxreg<R, TX, TY, ROLES>())) d2q9_batch_general
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) d2q9_outlet_chi_kernel(const __grid_constant__ D2Args<S, R> a) {
     __shared__ R s_chi;
+    grid_dep_wait();
     if (threadIdx.x < 32) {
         LamFold L;
         fold_begin(a, L, a.part_out, a.scal_out);
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(256) d2q9_outlet_chi_kernel(const __grid_const
     }
 }
 
-// FP64 mass / speed reduction for diagnostics.// FP64 mass / speed reduction for diagnostics.
+// FP64 mass / speed reduction for diagnostics.
 template <typename S, typename R>
 __global__ void __launch_bounds__(256) d2q9_diag_kernel(const S* __restrict__ f, const R* __restrict__ macro,
                                                         const uint16_t* __restrict__ info,

@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(MTX * MRB, 2)
     d2q9_march_kernel(const __grid_constant__ D2Args<float, float> a, const __grid_constant__ CUtensorMap tmap,
                       const int4* __restrict__ runs, const uint8_t* __restrict__ run_flags) {
     extern __shared__ __align__(128) unsigned char smraw[];
+    grid_dep_wait();
     // the launch asks for 128 bytes more than the layout: start it on a 128-byte boundary
     MarchSmem& sm = *reinterpret_cast<MarchSmem*>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -1,23 +1,28 @@
 // D3Q19 two-component MRT pseudopotential step with the corrected open faces
 // (the three-dimensional counterpart of lbm_d2q9.cu).
 //
-// One time step is three launches on the context's stream:
-//   A  d3q_pull_kernel    pull streaming (Eq. 2) with halfway bounce-back
-//                         (Eq. B1) and periodic wrap (Eq. B2); inlet
-//                         reconstruction (Eq. 13 over the 5 unknowns, alpha
-//                         correction Eqs. 15-19); convective outlet (Eq. 20);
-//                         component densities rho_k (= psi_k) to a field.
-//   B  d3q_collide_kernel rho and the solid indicator of a 32x4x2 tile plus a
-//                         2-node halo (ghost mirrors of Eqs. 24-25) staged in
-//                         shared memory; forces of Eqs. 10-11 on the 92-vector
-//                         8th-order isotropic stencil; common velocity
-//                         (Eqs. 7-8) with the outlet rescaled by chi (Eq. 22);
-//                         MRT collision with forcing (Eqs. 1, 3-6, 9) with the
-//                         19x19 transforms unrolled over compile-time
-//                         constants; per-face-node FP64 flux terms.
-//   C  d3q_reduce_kernel  fixed-order FP64 sums of the flux terms: lambda
-//                         (Eq. 21) and chi (Eq. 23) for the next step.
-// Face nodes carry their post-boundary populations from A to B, the outlet's
+// One time step is five launches on the context's stream:
+//   A  d3q_pull_kernel      pull streaming (Eq. 2) with halfway bounce-back
+//                           (Eq. B1) and periodic wrap (Eq. B2) of interior
+//                           nodes; component densities rho_k (= psi_k) to a
+//                           field.
+//   A' d3q_face_pull_kernel one thread per open-face slot: the same pull,
+//                           then inlet reconstruction (Eq. 13 over the 5
+//                           unknowns, alpha correction Eqs. 15-19) or the
+//                           convective outlet (Eq. 20); densities.
+//   B  d3q_collide_kernel   rho and the solid indicator of a 32x4xTZ tile plus
+//                           a 2-node halo (ghost mirrors of Eqs. 24-25) staged
+//                           in shared memory; forces of Eqs. 10-11 on the
+//                           92-vector 8th-order isotropic stencil; common
+//                           velocity (Eqs. 7-8); MRT collision with forcing
+//                           (Eqs. 1, 3-6, 9) with the 19x19 transforms
+//                           unrolled over compile-time constants; per-face-node
+//                           FP64 flux terms.
+//   B' d3q_outlet_kernel    outlet nodes: normal velocity chi times that of the
+//                           inward neighbour (Eq. 22), collision.
+//   C  d3q_reduce_kernel    fixed-order FP64 sums of the flux terms: lambda
+//                           (Eq. 21) and chi (Eq. 23) for the next step.
+// Face nodes carry their post-boundary populations from A' to B, the outlet's
 // previous post-boundary populations (Eq. 20) and the forces the inlet needs
 // one step later in small slot-indexed arrays.
 #include <cuda_fp16.h>
@@ -111,9 +116,19 @@ __device__ __forceinline__ void acc_c(R& acc, R v) {
 }
 
 // ---- tiles of the collide kernel -----------------------------------------
-constexpr int TX = 32, TY = 4, TZ = 2;
-constexpr int HX = TX + 4, HY = TY + 4, HZ = TZ + 4;
-constexpr int HN = HX * HY * HZ;
+// Tiles are TX x TY x TZ nodes; FP32 storage takes TZ = 4 (512 threads, two
+// CTAs per SM: a staged halo of 4.5 sites per node instead of 6.75), the
+// others TZ = 2 (FP64 needs 140 registers a thread, FP16 storage 80).
+constexpr int TX = 32, TY = 4;
+constexpr int HX = TX + 4, HY = TY + 4;
+template <typename S>
+struct Tile3 {
+    static constexpr int TZ = std::is_same<S, float>::value ? 4 : 2;
+    static constexpr int HZ = TZ + 4;
+    static constexpr int HN = HX * HY * HZ;
+    static constexpr int NT = TX * TY * TZ;
+    static constexpr int MIN_BLOCKS = sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 2 : 3);
+};
 
 template <typename R>
 struct Pair;
@@ -633,31 +648,40 @@ __device__ __forceinline__ void check_store_u(const D3Args<S>& a, long long n, t
     }
 }
 
-// Every fluid node of a 32x4x2 tile: forces from the staged densities (the
+// Every fluid node of a 32x4xTZ tile: forces from the staged densities (the
 // halo resolves periodic wraps and the ghost mirrors of Eqs. 24-25), the
 // common velocity, the collision.  Open-face nodes take their post-boundary
 // populations from the face kernel; outlet nodes stop after the force (their
 // normal velocity waits for the inward neighbour's, Eq. 22), and the inward
 // neighbours of the outlet hand theirs over with the flux terms of Eqs. 21, 23.
-// Residency: FP32 runs 4 CTAs of 256 per SM (64 registers, a few spilled
-// words; 7 % faster per step on GB300 than 3 CTAs at 80 registers), FP16
-// storage 3 (its decode needs more live values), FP64 1.
+// Residency: FP32 runs 2 CTAs of 512 per SM (64 registers, a few spilled
+// words), FP16 storage 3 of 256 (its decode needs more live values), FP64 1
+// of 256.  Tiles without a fluid node leave before staging.
 template <typename S>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 4 : 3)) d3q_collide_kernel(D3Args<S> a) {
+__global__ void __launch_bounds__(Tile3<S>::NT, Tile3<S>::MIN_BLOCKS) d3q_collide_kernel(D3Args<S> a) {
     using R = typename Store<S>::R;
+    constexpr int TZ = Tile3<S>::TZ, HN = Tile3<S>::HN, NT = Tile3<S>::NT;
     __shared__ typename Pair<R>::type s_rr[HN];  // (rho_1, rho_2) of the tile and its halo, psi = 0 at solids
     __shared__ __half2 s_ref[is_half<S>() ? HN : 1];  // FP16 storage: the same densities rounded to half
+    __shared__ R s_rate[2][Q];  // relaxation rates of both components (indexed by component below)
     // component 0's pulled populations, kept for its collision after
     // component 1's (FP32 arithmetic; FP64 pulls them again, its tile would
     // exceed the static shared-memory limit)
     constexpr bool STASH = sizeof(R) == 4;
-    __shared__ R s_f0[STASH ? Q : 1][STASH ? TX * TY * TZ : 1];
+    __shared__ R s_f0[STASH ? Q : 1][STASH ? NT : 1];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+    const bool in_grid = x < a.nx && y < a.ny && z < a.nz;
+    const long long n = in_grid ? node_index(a, x, y, z) : 0;
+    const uint32_t info = in_grid ? a.info[n] : (uint32_t)INFO3_SOLID;
+    // a tile without fluid nodes has nothing to stage or collide
+    if (!__syncthreads_or(!(info & INFO3_SOLID))) return;
+    if (tid < 2 * Q) s_rate[tid / Q][tid % Q] = a.s[tid / Q][tid % Q];
     // tiles whose halo lies inside the grid need no wrap / mirror / wall resolution
     const bool inner = x0 >= 2 && y0 >= 2 && z0 >= 2 && x0 + TX + 2 <= a.nx && y0 + TY + 2 <= a.ny &&
                        z0 + TZ + 2 <= a.nz;
-    for (int q = tid; q < HN; q += TX * TY * TZ) {
+    for (int q = tid; q < HN; q += NT) {
         const int hx = q % HX, hy = (q / HX) % HY, hz = q / (HX * HY);
         const long long m = inner ? node_index(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz)
                                   : site_index(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz);
@@ -669,11 +693,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 4 
         if constexpr (is_half<S>()) s_ref[q] = __floats2half2_rn((float)v.x, (float)v.y);
     }
     __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
-    if (x >= a.nx || y >= a.ny || z >= a.nz) return;
-    const long long n = node_index(a, x, y, z);
-    const uint32_t info = a.info[n];
-    if (info & INFO3_SOLID) return;
+    if (info & INFO3_SOLID) return;  // solid, or outside the grid
     const int hc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (threadIdx.z + 2));
     auto site = [&](int dx, int dy, int dz) { return s_rr[hc + dx + HX * (dy + HY * dz)]; };
     const int fid = (int)((info >> INFO3_FACE_SHIFT) & 7u);
@@ -760,25 +780,31 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 4 
         a.rref_out[a.plane + n] = __float2half_rn(r2);
     }
     // collide component 1 (still in registers), then component 0 (from the
-    // shared-memory copy in FP32, pulled again in FP64)
-    collide<R>(f, r2, u[0], u[1], u[2], F2[0], F2[1], F2[2], a.s[1]);
-    store_pop<S>(a, 1, n, f, dest_rho);
-    if (fid == 0) {
-        if constexpr (STASH)
-            static_for<0, Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                f[i] = s_f0[i][tid];
-            });
-        else pull<S, R>(a, 0, x, y, z, info, f);
-    } else {
-        const R* ff = a.fface + (size_t)slot * 2 * Q;
-        static_for<0, Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            f[i] = ff[i];
-        });
+    // shared-memory copy in FP32, pulled again in FP64): one loop body, so
+    // the unrolled collision is in the instruction stream once
+#pragma unroll 1
+    for (int k = 1; k >= 0; --k) {
+        if (k == 0) {
+            if (fid == 0) {
+                if constexpr (STASH)
+                    static_for<0, Q>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+                        f[i] = s_f0[i][tid];
+                    });
+                else pull<S, R>(a, 0, x, y, z, info, f);
+            } else {
+                const R* ff = a.fface + (size_t)slot * 2 * Q;
+                static_for<0, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    f[i] = ff[i];
+                });
+            }
+        }
+        const R rk = k ? r2 : r1;
+        const R fx = k ? F2[0] : F1[0], fy = k ? F2[1] : F1[1], fz = k ? F2[2] : F1[2];
+        collide<R>(f, rk, u[0], u[1], u[2], fx, fy, fz, s_rate[k]);
+        store_pop<S>(a, k, n, f, dest_rho);
     }
-    collide<R>(f, r1, u[0], u[1], u[2], F1[0], F1[1], F1[2], a.s[0]);
-    store_pop<S>(a, 0, n, f, dest_rho);
 }
 
 // One thread per outlet slot: the outlet node's velocity with the normal
@@ -955,6 +981,7 @@ cudaError_t launch_step(const D3Args<S>& a, cudaStream_t st, cudaEvent_t mid_a, 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (mid_a) cudaEventRecord(mid_a, st);
+    constexpr int TZ = Tile3<S>::TZ;
     const dim3 blkB(TX, TY, TZ);
     const dim3 grdB((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + TZ - 1) / TZ);
     d3q_collide_kernel<S><<<grdB, blkB, 0, st>>>(a);

@@ -19,7 +19,8 @@ LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_FP32, LBM_FP32_FP16STORE, LBM_FP64 = 0, 1, 2
 PRECISIONS = {"fp32": LBM_FP32, "fp16store": LBM_FP32_FP16STORE, "fp64": LBM_FP64}
 LBM_INLET_VELOCITY, LBM_OUTLET_CONVECTIVE = 1, 2
-SCHEDULES = {"graphs": 0, "persistent": 1}
+SCHEDULES = {"graphs": 0, "persistent": 1, "graphs_early": 2}
+SCHEDULE_NAMES = {v: k for k, v in SCHEDULES.items()}
 SIDES = {"xmin": 0, "xmax": 1, "ymin": 2, "ymax": 3, "zmin": 4, "zmax": 5}
 
 
@@ -121,6 +122,8 @@ def load():
     L.lbm_set_chi_timing.argtypes = [c_ctx, ctypes.c_int]
     L.lbm_set_schedule.restype = ctypes.c_int
     L.lbm_set_schedule.argtypes = [c_ctx, ctypes.c_int]
+    L.lbm_get_schedule.restype = ctypes.c_int
+    L.lbm_get_schedule.argtypes = [c_ctx, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.lbm_mass_noalloc.restype = ctypes.c_int
     L.lbm_mass_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -128,6 +131,8 @@ def load():
     L.lbm_batch_create.argtypes = [ctypes.POINTER(c_ctx), ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(c_ctx)]
     L.lbm_batch_set_schedule.restype = ctypes.c_int
     L.lbm_batch_set_schedule.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.lbm_batch_get_schedule.restype = ctypes.c_int
+    L.lbm_batch_get_schedule.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.lbm_batch_persistent_grid.restype = ctypes.c_int
     L.lbm_batch_persistent_grid.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
     L.lbm_batch_inject_barrier_fault.restype = ctypes.c_int
@@ -358,8 +363,14 @@ class Solver:
         _check(load().lbm_set_graph_mode(self.h, int(bool(on))), self.h)
 
     def set_schedule(self, name):
-        """'graphs' (default) or 'persistent' (lbm_set_schedule)."""
+        """'graphs' (default), 'graphs_early' or 'persistent' (lbm_set_schedule)."""
         _check(load().lbm_set_schedule(self.h, SCHEDULES[name]), self.h)
+
+    def schedule(self):
+        """(schedule name, whether the step graphs launch early) (lbm_get_schedule)."""
+        sch, early = ctypes.c_int(), ctypes.c_int()
+        _check(load().lbm_get_schedule(self.h, ctypes.byref(sch), ctypes.byref(early)), self.h)
+        return SCHEDULE_NAMES[sch.value], bool(early.value)
 
     def set_wall_velocity(self, side, ux):
         """Moving wall beyond the closed edge 'ymin' or 'ymax' (lbm_set_wall_velocity)."""
@@ -433,8 +444,14 @@ class Batch:
         self._check(load().lbm_batch_set_graph_mode(self.h, int(bool(on))))
 
     def set_schedule(self, name):
-        """'graphs' (default) or 'persistent' (lbm_batch_set_schedule)."""
+        """'graphs' (default), 'graphs_early' or 'persistent' (lbm_batch_set_schedule)."""
         self._check(load().lbm_batch_set_schedule(self.h, SCHEDULES[name]))
+
+    def schedule(self):
+        """(schedule name, whether the step graphs launch early) (lbm_batch_get_schedule)."""
+        sch, early = ctypes.c_int(), ctypes.c_int()
+        self._check(load().lbm_batch_get_schedule(self.h, ctypes.byref(sch), ctypes.byref(early)))
+        return SCHEDULE_NAMES[sch.value], bool(early.value)
 
     def persistent_grid(self):
         n = ctypes.c_int()

@@ -1,0 +1,144 @@
+"""D3Q19 physics beyond short-horizon parity (Sec. III C, Fig. 8): a droplet
+migrating through a walled duct with the corrected inlet and outlet, GPU
+against the FP64 D3Q19 oracle over a few thousand steps (droplet volume and
+centroid, component masses, chi, lambda), and the global mass variation of
+the paper-size duct (500 x 100 x 100) with and without the chi correction."""
+import numpy as np
+import pytest
+
+from oracle import oracle3d as O3
+from paper_2512_12934_gb300 import lbm
+from paper_2512_12934_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def droplet(rho, solid):
+    """Volume (nodes with rho_1 > rho_2), area-equivalent sphere diameter and
+    centroid (x, y, z) of the droplet."""
+    drop = (rho[0] > rho[1]) & (solid == 0)
+    zs, ys, xs = np.nonzero(drop)
+    V = float(drop.sum())
+    return V, 2.0 * (3.0 * V / (4.0 * np.pi)) ** (1.0 / 3.0), np.array([xs.mean(), ys.mean(), zs.mean()])
+
+
+def test_3d_droplet_migration_tracks_the_oracle():
+    # G12 = 1.6: at 1.2 a droplet of radius 6 dissolves into the continuous
+    # phase within 3000 steps (in the oracle as on the GPU); at 1.6 it keeps
+    # about 70% of its volume while it migrates ~40 nodes downstream.
+    w = W.duct3(nx=96, ny=22, nz=22, R=6.0, xc=24.0, u_max=0.02, G12=1.6, Gw=(0.2, -0.2))
+    s = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+    o = O3.Oracle3D(w.cfg, w.solid, w.rho, w.u, threads=16)
+    worst = {"D": 0.0, "xc": 0.0, "mass": 0.0, "chi": 0.0, "lambda": 0.0}
+    m0 = s.diagnostics()["mass"]
+    for _ in range(6):
+        s.step(500)
+        o.step(500)
+        d, so = s.diagnostics(), o.scalars()
+        assert d["status"] == 0
+        rg, _ = s.macros()
+        ro, _, _ = o.macros()
+        Vg, Dg, cg = droplet(rg, w.solid)
+        Vo, Do, co = droplet(ro, w.solid)
+        assert Vo > 0 and Vg > 0, "the droplet dissolved"
+        worst["D"] = max(worst["D"], abs(Dg / Do - 1))
+        worst["xc"] = max(worst["xc"], float(np.max(np.abs(cg - co))))
+        worst["mass"] = max(worst["mass"], float(np.max(np.abs(d["mass"] - so["mass"]) / so["mass"])))
+        worst["chi"] = max(worst["chi"], abs(d["chi"] - so["chi"]))
+        worst["lambda"] = max(worst["lambda"], abs(d["lambda"] / so["lambda"] - 1))
+    dev_g = (d["mass"].sum() - m0.sum()) / m0.sum()
+    dev_o = (so["mass"].sum() - m0.sum()) / m0.sum()
+    print("\n[3d migration] worst over 6 checkpoints: " + ", ".join("%s %.2e" % kv for kv in worst.items()) +
+          "; total-mass deviation gpu %.3e oracle %.3e" % (dev_g, dev_o))
+    assert worst["D"] <= 0.01 and worst["xc"] <= 0.5
+    assert worst["mass"] <= 1e-5 and worst["chi"] <= 2e-3 and worst["lambda"] <= 2e-3
+    assert abs(dev_g - dev_o) <= 0.01 * max(abs(dev_o), 1e-4)
+
+
+def test_paper_size_duct_mass_variation_with_and_without_chi():
+    """500 x 100 x 100 duct (Fig. 8), droplet R = 20 at x = 100: the total
+    mass stays closer to its initial value with the chi correction."""
+    dev = {}
+    for chi in (True, False):
+        w = W.duct3(nx=500, ny=100, nz=100, R=20.0, xc=100.0, u_max=0.01, G12=1.2, Gw=(0.2, -0.2), chi=chi)
+        s = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+        m0 = s.diagnostics()["mass"].sum()
+        track = []
+        for _ in range(8):
+            s.step(1000)
+            d = s.diagnostics()
+            assert d["status"] == 0
+            track.append(abs(d["mass"].sum() / m0 - 1))
+        dev[chi] = (max(track), track)
+        s.close()
+    print("\n[3d duct 500x100x100] max |m/m0 - 1| over 8k steps: chi on %.3e, off %.3e" % (dev[True][0], dev[False][0]))
+    assert dev[True][0] < dev[False][0]
+
+
+def components(rho, solid):
+    """Connected regions of the dispersed phase (rho_1 > rho_2) as (volume,
+    x_min, x_max, centroid x), ordered by x_min."""
+    from scipy import ndimage
+
+    drop = (rho[0] > rho[1]) & (solid == 0)
+    lab, n = ndimage.label(drop)
+    out = []
+    for j in range(1, n + 1):
+        xs = np.nonzero(lab == j)[2]
+        out.append((int(xs.size), int(xs.min()), int(xs.max()), float(xs.mean())))
+    return sorted(out, key=lambda c: c[1])
+
+
+def test_coflow_device_drips_at_low_and_jets_at_high_continuous_speed():
+    """The config-3 coaxial device (Sec. III D, Figs. 10-11; 384 long here,
+    bore w_d = 24).  At u_c = 0.01 the dispersed thread grows from the
+    nozzle, necks and pinches off (dripping, Fig. 10(b)): the attached
+    thread's volume grows monotonically until the pinch-off, then drops, and
+    the detached droplet travels downstream keeping its volume.  At u_c =
+    0.02 (same flow-rate ratio) the thread reaches the outlet without
+    breaking upstream of it (jetting, the regime of Fig. 11)."""
+    pytest.importorskip("scipy")
+    nozzle, wd = 48, 24.0
+    w = W.coflow3(nx=384, u_c=0.01)
+    s = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+    attached, detached = [], []
+    for k in range(12):
+        s.step(2000)
+        assert s.diagnostics()["status"] == 0
+        rho, _ = s.macros()
+        comps = components(rho, w.solid)
+        thread = [c for c in comps if c[1] == 0]
+        assert len(thread) == 1, "the dispersed thread must stay connected to the inlet"
+        attached.append(thread[0][0])
+        free = [c for c in comps if c[1] > nozzle + 4 and c[2] < w.cfg["nx"] - 1]
+        detached.append(max(free) if free else None)
+    s.close()
+    first = next((k for k, d in enumerate(detached) if d is not None), None)
+    d_eq = lambda V: 2.0 * (3.0 * V / (4.0 * np.pi)) ** (1.0 / 3.0) / wd
+    print("\n[coflow u_c 0.01] attached-thread D/w_d every 2000 steps: " +
+          " ".join("%.2f" % d_eq(V) for V in attached) +
+          "; first detached droplet at step %s: " % (None if first is None else 2000 * (first + 1)) +
+          ("D/w_d %.2f" % d_eq(detached[first][0]) if first is not None else "none"))
+    assert first is not None and first >= 2, "no pinch-off within 24000 steps"
+    assert all(attached[k + 1] > attached[k] for k in range(first - 1)), "the thread must grow until pinch-off"
+    assert attached[first] < 0.7 * attached[first - 1], "pinch-off must take volume from the thread"
+    track = [d for d in detached[first:] if d is not None]
+    assert len(track) >= 2
+    assert all(track[k + 1][3] > track[k][3] for k in range(len(track) - 1)), "the droplet must move downstream"
+    assert abs(track[-1][0] / track[0][0] - 1.0) < 0.08
+
+    w = W.coflow3(nx=384, u_c=0.02)
+    s = lbm.Solver(w.cfg, w.solid, w.rho, w.u)
+    reached = False
+    for k in range(6):
+        s.step(2000)
+        assert s.diagnostics()["status"] == 0
+        rho, _ = s.macros()
+        comps = components(rho, w.solid)
+        assert not [c for c in comps if c[1] > nozzle + 4 and c[2] < w.cfg["nx"] - 16], \
+            "u_c = 0.02 must not drip upstream of the outlet"
+        thread = [c for c in comps if c[1] == 0]
+        reached = reached or (len(thread) == 1 and thread[0][2] == w.cfg["nx"] - 1)
+    s.close()
+    print("[coflow u_c 0.02] jetting: thread reached the outlet within 12000 steps: %s" % reached)
+    assert reached
