@@ -285,7 +285,8 @@ def batched_vs_sequential(n, steps, reps, precision, stream_handle, world=1, ran
 # forward 2(4*128 + 2*128^2 + 128*2); backward 4*2*128 + 8*128^2 + 2*128*4.
 MLP_FWD_FLOP = 2 * (4 * 128 + 2 * 128 * 128 + 128 * 2)
 MLP_BWD_FLOP = 4 * 2 * 128 + 8 * 128 * 128 + 2 * 128 * 4
-# FP32 FMA peak of the SIMT pipes: 152 SMs x 128 lanes x 2 FLOP at 2070 MHz.
+
+
 def accuracy_figures(stream_handle):
     """The paper's headline accuracy quantities, measured with the FP32 GPU
     path (context, not a target; quoted beside the paper's own figures).
@@ -349,7 +350,20 @@ def accuracy_figures(stream_handle):
                      "mass: 1024x128 channel, 50k steps"}
 
 
+# FP32 FMA peak of the SIMT pipes: 152 SMs x 128 lanes x 2 FLOP at 2070 MHz.
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def split_tensor_peak():
+    """Peak of the tensor-core inference path in FP32-equivalent FLOP/s: each
+    hidden-layer FLOP is one TF32 product Ah.Wh, one TF32 product Al.Wh and
+    one BF16 product Ab.Wl; TF32 runs at half the BF16 rate (2.25 against
+    1.1 PFLOP/s dense, nominal), so the tensor pipes deliver the measured
+    burst BF16 rate / (2 * 2 + 1)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["bf16_tflops"]) / 5.0, "measured bf16_tflops (burst) / 5"
+    return 1900.0 / 5.0, "fallback bf16 1.9 PFLOP/s / 5"
 
 
 def coflow3d(precision, stream_handle, bench_steps, lbm_steps, warmup, e2e=True):
@@ -440,8 +454,10 @@ def surrogate_cpu_baseline(solver_s_per_point, n=4096, members=5):
 
 def mlp_kernels(stream_handle, n_infer=65536, n_train=4096, members=5, reps=10):
     """Device-resident timings of the surrogate kernels: ensemble inference on
-    n_infer points (forward + mean/spread) and Adam training steps on
-    n_train samples (forward + backward + update), against the FP32 ALU peak."""
+    n_infer points (forward + mean/spread) on the tensor-core path (default)
+    against the split-product tensor peak and on the FP32 path against the
+    FP32 ALU peak, and Adam training steps on n_train samples (forward +
+    backward + update, FP32 pipes)."""
     import numpy as np
     import torch
 
@@ -453,16 +469,22 @@ def mlp_kernels(stream_handle, n_infer=65536, n_train=4096, members=5, reps=10):
         X = torch.from_numpy(rng.standard_normal((n_infer, 4)).astype(np.float32)).cuda()
         mean = torch.empty((n_infer, 2), dtype=torch.float32, device="cuda")
         spread = torch.empty(n_infer, dtype=torch.float32, device="cuda")
-        net.predict_device(X.data_ptr(), n_infer, mean.data_ptr(), spread.data_ptr())
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         st = torch.cuda.current_stream()
-        ev0.record(st)
-        for _ in range(reps):
+
+        def time_infer(path):
+            net.set_infer_path(path)
             net.predict_device(X.data_ptr(), n_infer, mean.data_ptr(), spread.data_ptr())
-        ev1.record(st)
-        torch.cuda.synchronize()
-        t_inf = ev0.elapsed_time(ev1) / 1e3 / reps
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(st)
+            for _ in range(reps):
+                net.predict_device(X.data_ptr(), n_infer, mean.data_ptr(), spread.data_ptr())
+            ev1.record(st)
+            torch.cuda.synchronize()
+            return ev0.elapsed_time(ev1) / 1e3 / reps
+
+        t_simt = time_infer("simt")
+        t_inf = time_infer("tensor")
         Xt = rng.standard_normal((n_train, 4)).astype(np.float32)
         Tt = rng.standard_normal((n_train, 2)).astype(np.float32)
         net.train(Xt, Tt, epochs=2, batch=n_train, lr=1e-3)
@@ -472,10 +494,16 @@ def mlp_kernels(stream_handle, n_infer=65536, n_train=4096, members=5, reps=10):
     finally:
         net.close()
     inf_tf = n_infer * members * MLP_FWD_FLOP / t_inf / 1e12
+    simt_tf = n_infer * members * MLP_FWD_FLOP / t_simt / 1e12
     tr_tf = n_train * members * (MLP_FWD_FLOP + MLP_BWD_FLOP) / t_step / 1e12
+    tpk, tpk_src = split_tensor_peak()
     return {"members": members,
-            "infer_points": n_infer, "infer_ms": t_inf * 1e3, "infer_points_per_s": n_infer / t_inf,
-            "infer_tflops": inf_tf, "infer_frac_of_fp32_alu_peak": inf_tf / FP32_ALU_PEAK_TFLOPS,
+            "infer_points": n_infer, "infer_path": "tensor (tcgen05, 3-term split product)",
+            "infer_ms": t_inf * 1e3, "infer_points_per_s": n_infer / t_inf,
+            "infer_tflops": inf_tf, "infer_frac_of_split_tensor_peak": inf_tf / tpk,
+            "split_tensor_peak_tflops": tpk, "split_tensor_peak_source": tpk_src,
+            "infer_simt_ms": t_simt * 1e3, "infer_simt_tflops": simt_tf,
+            "infer_simt_frac_of_fp32_alu_peak": simt_tf / FP32_ALU_PEAK_TFLOPS,
             "train_samples": n_train, "train_step_ms": t_step * 1e3, "train_tflops": tr_tf,
             "train_frac_of_fp32_alu_peak": tr_tf / FP32_ALU_PEAK_TFLOPS,
             "fp32_alu_peak_tflops": FP32_ALU_PEAK_TFLOPS,
@@ -691,10 +719,11 @@ def main():
                 "config": {"workload": "tjunction_surrogate", "members": 5, "network": "4-128-128-128-2 GELU",
                            "inference_batch": 65536, "train_runs": args.sur_train, "test_runs": args.sur_test},
                 "surrogate": res,
-                "roofline": {"bound": "alu", "achieved": kern["infer_tflops"],
-                             "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": kern["infer_frac_of_fp32_alu_peak"], "traffic": None,
-                             "kernel": "mlp_forward_kernel + mlp_reduce_kernel (65536 points x 5 members)"},
+                "roofline": {"bound": "tensor", "achieved": kern["infer_tflops"],
+                             "peak": kern["split_tensor_peak_tflops"], "unit": "TFLOP/s",
+                             "frac": kern["infer_frac_of_split_tensor_peak"], "traffic": None,
+                             "peak_source": kern["split_tensor_peak_source"],
+                             "kernel": "mlp_infer_tc_kernel + mlp_reduce_kernel (65536 points x 5 members)"},
                 "mlp_kernels": kern,
                 "e2e": {"value": res["speedup_host"], "unit": "x", "h2d_bytes_per_step": 65536 * 4 * 4,
                         "d2h_bytes_per_step": 65536 * 3 * 4,

@@ -425,7 +425,9 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  * ratio, the viscosity ratio and the width ratio (Sec. 4, Figs. 10-11); the
  * surrogate learns that map from runs of this solver.
  * Network of one member: x (4) -> 128 -> 128 -> 128 -> y (2), GELU
- * (z * Phi(z), the erf form) after each hidden layer, FP32 throughout.
+ * (z * Phi(z), the erf form) after each hidden layer, FP32 arithmetic
+ * (inference by default on the tensor cores, as FP32-accurate split
+ * products: lbm_mlp_set_infer_path).
  * Loss: mean squared error over the batch and both outputs.  Optimiser: Adam
  * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).
  * Parameters of one member, flat float order (row-major, output index
@@ -450,7 +452,9 @@ lbm_status lbm_mlp_set_params(lbm_mlp* m, const float* params);
 /* Copy all members' parameters out (host, members*num_params floats). */
 lbm_status lbm_mlp_get_params(lbm_mlp* m, float* params);
 
-/* Every member's output on n inputs: Y [members][n][2] (host). */
+/* Every member's output on n inputs: Y [members][n][2] (host).  On the
+ * tensor-core path a bounded device wait that ran out returns
+ * LBM_ERR_TIMEOUT (outputs undefined; the ensemble stays usable). */
 lbm_status lbm_mlp_forward(lbm_mlp* m, const float* X, int n, float* Y);
 
 /* Full-batch gradient of every member's loss on (X, T): grad
@@ -469,6 +473,27 @@ lbm_status lbm_mlp_train(lbm_mlp* m, const float* X, const float* T, int n, int 
  * dst_is_device != 0: X, mean and spread are device pointers on the
  * library's device (enqueued on the stream, still waited for). */
 lbm_status lbm_mlp_predict(lbm_mlp* m, const float* X, int n, float* mean, float* spread, int dst_is_device);
+
+/* Inference paths of lbm_mlp_forward and lbm_mlp_predict (training always
+ * runs on the FP32 pipes).
+ *  LBM_MLP_INFER_SIMT: FP32 FMAs, 128-sample tiles with 8x8 register blocks.
+ *  LBM_MLP_INFER_TENSOR (default): the two 128x128 hidden layers on the tcgen05
+ *    tensor cores as three accumulated products, tf32(A).tf32(W) +
+ *    (A - tf32(A)).tf32(W) + bf16(A).bf16(W - tf32(W)), which keeps FP32-level
+ *    error (below 2^-20 of |A||W| per product); layers 1 and 4, biases and
+ *    GELU on the FP32 pipes.  Results differ from the SIMT path in the last
+ *    bits (another summation order).
+ * Waits for the ensemble's stream. */
+enum { LBM_MLP_INFER_SIMT = 0, LBM_MLP_INFER_TENSOR = 1 };
+lbm_status lbm_mlp_set_infer_path(lbm_mlp* m, int path);
+
+/* Longest wait, in SM clock cycles, of the tensor-core inference kernel on
+ * its weight copy and on its MMAs (0: the default, about a second).  A wait
+ * that runs out ends the call with LBM_ERR_TIMEOUT; the kernel lets its own
+ * weight copy land (default limit) and frees its tensor memory before it
+ * leaves, so the ensemble stays usable.  Small limits exist to exercise
+ * that path.  Waits for the ensemble's stream. */
+lbm_status lbm_mlp_set_wait_limit(lbm_mlp* m, long long cycles);
 
 /* Release the ensemble.  NULL is ignored. */
 void lbm_mlp_destroy(lbm_mlp* m);

@@ -1,5 +1,7 @@
 // Surrogate MLP ensemble (4 -> 128 -> 128 -> 128 -> 2, GELU), FP32, with
-// fused forward, backward and Adam kernels.
+// fused forward, backward and Adam kernels, and an inference kernel that
+// runs the two hidden layers on the tcgen05 tensor cores (FP32-accurate
+// split products; the default inference path).
 //
 // One CTA owns TILE samples of one ensemble member.  Forward: the four layers
 // run back to back on activations held in shared memory; each 128x128 weight
@@ -8,6 +10,7 @@
 // tile (output error, dZ3, dW3, dA2, dZ2, dW2, dA1, dZ1, dW1 and the biases)
 // stays on chip; the tile writes its gradient partial with plain stores.  Adam
 // sums the tiles' partials in a fixed order (deterministic) and updates.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -398,6 +401,302 @@ __global__ void __launch_bounds__(NTB) mlp_infer_kernel(const float* __restrict_
     }
 }
 
+// ---- inference on the tensor cores (tcgen05) ------------------------------
+// The two hidden layers are D = A . W^T on 128-sample tiles (M = 128 samples,
+// N = 128 neurons, K = 128), with A the previous layer's activations and W
+// the layer's weight matrix [neuron][input].  FP32 accuracy from three
+// products accumulated into one FP32 D in tensor memory:
+//   A . W^T  ~  Ah . Wh^T + Al . Wh^T + Ab . Wl^T
+// with Ah = tf32(A), Al = A - Ah, Wh = tf32(W) (the first two on kind::tf32,
+// where Al is truncated to TF32 by the unit), Wl = bf16(W - Wh) and
+// Ab = bf16(A) (kind::f16 with bf16 operands).  The dropped Al . Wl term and
+// the roundings of the third product are below 2^-20 of |A||W|.
+// Activations go to tensor memory (tcgen05.st, the MMA's A operand); the
+// weights of both layers of the CTA's member sit in shared memory in the
+// no-swizzle K-major layout (8-row x 16-byte core matrices, the next core
+// matrix along K 128 bytes on, the next 8 rows (K * bytes / 16) * 128 bytes
+// on), copied in by one bulk copy of the member's prepared image.  Layers 1
+// (K = 4) and 4 (N = 2), the biases and GELU run on the FP32 pipes in the
+// epilogues; thread (w, l) owns sample 32 (w % 4) + l (its TMEM lane) and
+// the 32 neurons of column quarter w / 4.
+constexpr int TCT = 512;
+constexpr int TC_WH = H * H * 4, TC_WL = H * H * 2, TC_LAYER = TC_WH + TC_WL, TC_IMG = 2 * TC_LAYER;
+constexpr size_t TC_SMEM = (size_t)TC_IMG + 128;
+constexpr unsigned MLP_TC_TIMEOUT = 1u;
+
+__host__ __device__ inline int tc_canon(int r, int k, int esize) {
+    const int E = 16 / esize;
+    return (r / 8) * ((H / E) * 128) + (k / E) * 128 + (r % 8) * 16 + (k % E) * esize;
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// img[e][l] = { Wh (TF32 values in FP32 containers), Wl (bf16) } of hidden
+// layer l + 2, both in the shared-memory layout above.
+__global__ void mlp_tc_prep_kernel(const float* __restrict__ params, unsigned char* __restrict__ img) {
+    const int e = blockIdx.y;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;  // over 2 * H * H
+    if (q >= 2 * H * H) return;
+    const int l = q / (H * H), r = q % (H * H), j = r / H, k = r % H;
+    const float w = params[(size_t)e * PS + (l ? oW3 : oW2) + j * H + k];
+    const float wh = tf32_rna(w);
+    unsigned char* base = img + (size_t)e * TC_IMG + (size_t)l * TC_LAYER;
+    *reinterpret_cast<float*>(base + tc_canon(j, k, 4)) = wh;
+    *reinterpret_cast<__nv_bfloat16*>(base + TC_WH + tc_canon(j, k, 2)) = __float2bfloat16_rn(w - wh);
+}
+
+__device__ __forceinline__ uint32_t tc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t sbo) {
+    // start >> 4, leading byte offset 128 >> 4, stride byte offset >> 4,
+    // descriptor version 1 (bit 46), no swizzle
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// instruction descriptor of kind::tf32 (fmt 2) / kind::f16 with bf16 (fmt 1):
+// FP32 D, K-major A and B, N = 128, M = 128
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(H >> 3) << 17) | ((uint32_t)(TB >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(bool tf32, uint32_t d, uint32_t a, uint64_t b, uint32_t id, int acc) {
+    if (tf32)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+                     :: "r"(d), "r"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+    else
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+                     :: "r"(d), "r"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void tc_st16(uint32_t t, const uint32_t (&v)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+                 :: "r"(t), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+                    "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) : "memory");
+}
+__device__ __forceinline__ void tc_st8(uint32_t t, const uint32_t (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "r"(t), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]) : "memory");
+}
+__device__ __forceinline__ void tc_ld16(uint32_t t, uint32_t (&v)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                 : "r"(t) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Bounded wait on phase `parity` of an mbarrier; false (and the status bit)
+// if it did not complete within `limit` SM clock cycles.
+constexpr long long TC_WAIT_LIMIT = 2000000000LL;  // about a second at 2 GHz
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, unsigned* status, long long limit) {
+    const long long t0 = clock64();
+    for (;;) {
+        // test_wait does not suspend: the limit counts from the first probe
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(tc_smem(bar)), "r"(parity) : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) {
+            atomicOr(status, MLP_TC_TIMEOUT);
+            return false;
+        }
+        __nanosleep(20);
+    }
+}
+
+__device__ __forceinline__ void tc_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// The activations a[16] of neurons j0..j0+15 (j0 even) of this thread's
+// sample as the next MMA's A operand: Ah, Al (one column each) and Ab (two
+// per column, the even neuron in the low half).
+__device__ __forceinline__ void tc_put_act(uint32_t tAh, uint32_t tAl, uint32_t tAb, int j0, const float (&a)[16]) {
+    uint32_t h[16], lo[16], b2[8];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float ah = tf32_rna(a[i]);
+        h[i] = __float_as_uint(ah);
+        lo[i] = __float_as_uint(a[i] - ah);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 pr = __floats2bfloat162_rn(a[2 * i], a[2 * i + 1]);  // .x = low half
+        b2[i] = *reinterpret_cast<const uint32_t*>(&pr);
+    }
+    tc_st16(tAh + j0, h);
+    tc_st16(tAl + j0, lo);
+    tc_st8(tAb + j0 / 2, b2);
+}
+
+// Persistent per member: CTA (x, e) loads member e's weights once and runs
+// tiles x, x + gridDim.x, ... of that member.
+__global__ void __launch_bounds__(TCT, 1) mlp_infer_tc_kernel(const float* __restrict__ params,
+                                                              const unsigned char* __restrict__ img,
+                                                              const float* __restrict__ X, int B,
+                                                              float* __restrict__ Y, unsigned* status,
+                                                              long long limit) {
+    extern __shared__ __align__(128) unsigned char tc_raw[];
+    unsigned char* sw = tc_raw + ((128u - (tc_smem(tc_raw) & 127u)) & 127u);
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[2];  // [0] weights landed, [1] MMAs of a layer done
+    __shared__ float s_w1[H * I], s_b[3][H], s_w4[O * H], s_b4[O];
+    __shared__ float s_part[4][O][TB];
+    __shared__ int s_ok, s_mma_pending;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = warp & 3, qc = warp >> 2;
+    const int row = 32 * g + lane, j0 = 32 * qc;
+    const int e = blockIdx.y, ntiles = (B + TB - 1) / TB;
+    const float* p = params + (size_t)e * PS;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc_smem(&s_bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc_smem(&s_bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
+        s_mma_pending = -1;
+    }
+    __syncthreads();
+    bool weights = false;  // thread 0: the weight image has landed
+    if (tid == 0) {
+        // the member's weight image: four bulk copies onto one transaction count
+        const unsigned char* src = img + (size_t)e * TC_IMG;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(tc_smem(&s_bar[0])), "r"(TC_IMG) : "memory");
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(tc_smem(sw + c * (TC_IMG / 4))), "l"(src + c * (TC_IMG / 4)), "r"(TC_IMG / 4),
+                            "r"(tc_smem(&s_bar[0])) : "memory");
+        // the other threads stage the small parameters and run layer 1 meanwhile
+        weights = tc_wait(&s_bar[0], 0, status, limit);
+        if (!weights) s_ok = 0;
+    }
+    for (int i = tid; i < H * I; i += TCT) s_w1[i] = p[oW1 + i];
+    for (int i = tid; i < H; i += TCT) {
+        s_b[0][i] = p[ob1 + i];
+        s_b[1][i] = p[ob2 + i];
+        s_b[2][i] = p[ob3 + i];
+    }
+    for (int i = tid; i < O * H; i += TCT) s_w4[i] = p[oW4 + i];
+    if (tid < O) s_b4[tid] = p[ob4 + tid];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(tc_smem(&s_tmem)), "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_sync();
+    const uint32_t lane_off = (uint32_t)(32 * g) << 16;
+    const uint32_t tD = s_tmem + lane_off, tAh = tD + 128, tAl = tD + 256, tAb = tD + 384;
+#pragma unroll 1
+    for (int t = blockIdx.x; t < ntiles && s_ok; t += gridDim.x) {
+        const int b = t * TB + row;
+        // ---- layer 1 (K = 4) on the FP32 pipes, GELU, A of layer 2 ----
+        {
+            float x[I] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (b < B)
+#pragma unroll
+                for (int k = 0; k < I; ++k) x[k] = __ldg(X + (size_t)b * I + k);
+#pragma unroll
+            for (int c = 0; c < 32; c += 16) {
+                float a[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int j = j0 + c + i;
+                    float z = s_b[0][j];
+#pragma unroll
+                    for (int k = 0; k < I; ++k) z = fmaf(s_w1[j * I + k], x[k], z);
+                    a[i] = gelu(z);
+                }
+                tc_put_act(tAh, tAl, tAb, j0 + c, a);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+#pragma unroll 1
+        for (int l = 0; l < 2; ++l) {
+            tc_sync();
+            if (tid == 0) {
+                // 40 MMAs of the layer from one thread; a K step moves the
+                // descriptor's start address by 256 bytes (+16 in its field)
+                const uint32_t wh = tc_smem(sw + l * TC_LAYER), wl = wh + TC_WH;
+                const uint32_t it = tc_idesc(2), ib = tc_idesc(1);
+                const uint32_t d = s_tmem, ah = s_tmem + 128, al = s_tmem + 256, ab = s_tmem + 384;
+                const uint64_t dh = tc_desc(wh, (H / 4) * 128), dl = tc_desc(wl, (H / 8) * 128);
+#pragma unroll
+                for (int s = 0; s < H / 8; ++s) tc_mma(true, d, ah + 8 * s, dh + 16 * s, it, s > 0);
+#pragma unroll
+                for (int s = 0; s < H / 8; ++s) tc_mma(true, d, al + 8 * s, dh + 16 * s, it, 1);
+#pragma unroll
+                for (int s = 0; s < H / 16; ++s) tc_mma(false, d, ab + 8 * s, dl + 16 * s, ib, 1);
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(tc_smem(&s_bar[1])) : "memory");
+                s_mma_pending = l;
+            }
+            __syncthreads();
+            // two commits per tile: phase parity = layer
+            // one decision for the whole CTA: every thread saw the phase complete
+            const int ok_before = s_ok;
+            if (!__syncthreads_and(ok_before && tc_wait(&s_bar[1], (uint32_t)l, status, limit))) {
+                if (tid == 0) s_ok = 0;
+                break;
+            }
+            if (tid == 0) s_mma_pending = -1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (l == 0) {
+                // ---- epilogue of layer 2: bias, GELU, A of layer 3 ----
+#pragma unroll
+                for (int c = 0; c < 32; c += 16) {
+                    uint32_t v[16];
+                    tc_ld16(tD + j0 + c, v);
+                    float a[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) a[i] = gelu(__uint_as_float(v[i]) + s_b[1][j0 + c + i]);
+                    tc_put_act(tAh, tAl, tAb, j0 + c, a);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            } else {
+                // ---- epilogue of layer 3 and layer 4 (N = 2): partial sums over this quarter ----
+                float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 32; c += 16) {
+                    uint32_t v[16];
+                    tc_ld16(tD + j0 + c, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int j = j0 + c + i;
+                        const float a = gelu(__uint_as_float(v[i]) + s_b[2][j]);
+                        y0 = fmaf(a, s_w4[j], y0);
+                        y1 = fmaf(a, s_w4[H + j], y1);
+                    }
+                }
+                s_part[qc][0][row] = y0;
+                s_part[qc][1][row] = y1;
+            }
+        }
+        tc_sync();
+        if (s_ok && tid < O * TB) {
+            const int r = tid % TB, o = tid / TB, bb = t * TB + r;
+            const float y = s_b4[o] + ((s_part[0][o][r] + s_part[1][o][r]) + (s_part[2][o][r] + s_part[3][o][r]));
+            if (bb < B) Y[((size_t)e * B + bb) * O + o] = y;
+        }
+    }
+    // a weight copy or MMAs still in flight (their wait ran out) complete
+    // before the CTA frees its tensor memory and leaves
+    tc_sync();
+    if (tid == 0) {
+        if (!weights) tc_wait(&s_bar[0], 0, status, TC_WAIT_LIMIT);
+        if (s_mma_pending >= 0) tc_wait(&s_bar[1], (uint32_t)s_mma_pending, status, TC_WAIT_LIMIT);
+    }
+    tc_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(s_tmem), "r"(512) : "memory");
+}
+
 // Ensemble mean and relative spread (max over outputs of the population std
 // over members / |mean|), two passes over the members.
 __global__ void mlp_reduce_kernel(const float* __restrict__ Y, int E, int B, float* __restrict__ mean,
@@ -441,6 +740,11 @@ struct lbm_mlp {
     int64_t t = 0;            // Adam steps taken
     uint64_t seed = 0;
     float* wt = nullptr;      // [E][2][H][H] k-major copy of the hidden weights (inference)
+    unsigned char* tcimg = nullptr;  // [E][TC_IMG] tensor-core images of the hidden weights
+    unsigned* status = nullptr;      // device status word of the tensor-core inference
+    int infer_path = LBM_MLP_INFER_TENSOR;
+    int sms = 1;  // SMs of the device (persistent tensor-core grid)
+    long long wait_limit = TC_WAIT_LIMIT;  // SM cycles a tensor-core wait may take
     void* ws = nullptr;       // grow-only device workspace of the per-call buffers
     size_t ws_bytes = 0;
     std::string err;
@@ -476,6 +780,9 @@ cudaError_t set_smem_attrs() {
         if (g_attr_err == cudaSuccess)
             g_attr_err = cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)SMEM_BYTES);
+        if (g_attr_err == cudaSuccess)
+            g_attr_err = cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)TC_SMEM);
     });
     return g_attr_err;
 }
@@ -547,12 +854,35 @@ lbm_status run_step(lbm_mlp* mm, Scratch& s, int B, const int* idx, bool adam, d
 lbm_status refresh_wt(lbm_mlp* mm) {
     mlp_transpose_kernel<<<dim3((2 * H * H + 255) / 256, mm->E), 256, 0, mm->stream>>>(mm->params, mm->wt);
     MCK(cudaGetLastError());
+    mlp_tc_prep_kernel<<<dim3((2 * H * H + 255) / 256, mm->E), 256, 0, mm->stream>>>(mm->params, mm->tcimg);
+    MCK(cudaGetLastError());
     return LBM_OK;
 }
 
 lbm_status launch_infer(lbm_mlp* mm, const float* dX, int n, float* dY) {
-    mlp_infer_kernel<<<dim3((n + TB - 1) / TB, mm->E), NTB, SMEM_BIG, mm->stream>>>(mm->params, mm->wt, dX, n, dY);
+    if (mm->infer_path == LBM_MLP_INFER_TENSOR) {
+        // persistent per member: about one CTA per SM over all members
+        const int ntiles = (n + TB - 1) / TB;
+        const int per = std::max(1, std::min(ntiles, mm->sms / mm->E));
+        mlp_infer_tc_kernel<<<dim3(per, mm->E), TCT, TC_SMEM, mm->stream>>>(mm->params, mm->tcimg, dX, n, dY,
+                                                                             mm->status, mm->wait_limit);
+    } else {
+        mlp_infer_kernel<<<dim3((n + TB - 1) / TB, mm->E), NTB, SMEM_BIG, mm->stream>>>(mm->params, mm->wt, dX, n,
+                                                                                          dY);
+    }
     MCK(cudaGetLastError());
+    return LBM_OK;
+}
+
+// After the stream has drained: a tensor-core wait that ran out is an error
+// (the outputs of that call are undefined); the word is cleared for the next.
+lbm_status check_infer(lbm_mlp* mm) {
+    unsigned st = 0;
+    MCK(cudaMemcpy(&st, mm->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st) {
+        MCK(cudaMemset(mm->status, 0, sizeof(unsigned)));
+        return mfail(mm, LBM_ERR_TIMEOUT, "a tensor-core wait of the inference kernel ran out; outputs undefined");
+    }
     return LBM_OK;
 }
 
@@ -572,6 +902,9 @@ lbm_status lbm_mlp_create(int members, uint64_t seed, void* cuda_stream, lbm_mlp
     mm->stream = static_cast<cudaStream_t>(cuda_stream);
     mm->seed = seed;
     cudaError_t e = set_smem_attrs();
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mm->sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t bytes = (size_t)members * PS * sizeof(float);
     if (e == cudaSuccess) e = cudaMalloc((void**)&mm->params, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&mm->m, bytes);
@@ -579,6 +912,9 @@ lbm_status lbm_mlp_create(int members, uint64_t seed, void* cuda_stream, lbm_mlp
     if (e == cudaSuccess) e = cudaMemset(mm->m, 0, bytes);
     if (e == cudaSuccess) e = cudaMemset(mm->v, 0, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&mm->wt, (size_t)members * 2 * H * H * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&mm->tcimg, (size_t)members * TC_IMG);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&mm->status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(mm->status, 0, sizeof(unsigned));
     if (e != cudaSuccess) {
         const std::string msg = std::string("mlp allocation: ") + cudaGetErrorString(e);
         lbm_mlp_destroy(mm);
@@ -643,7 +979,7 @@ lbm_status lbm_mlp_forward(lbm_mlp* mm, const float* X, int n, float* Y) {
     if (st != LBM_OK) return st;
     MCK(cudaMemcpyAsync(Y, s.Y, (size_t)mm->E * n * O * sizeof(float), cudaMemcpyDeviceToHost, mm->stream));
     MCK(cudaStreamSynchronize(mm->stream));
-    return LBM_OK;
+    return check_infer(mm);
 }
 
 lbm_status lbm_mlp_gradient(lbm_mlp* mm, const float* X, const float* T, int n, float* grad) {
@@ -715,13 +1051,30 @@ lbm_status lbm_mlp_predict(lbm_mlp* mm, const float* X, int n, float* mean, floa
         MCK(cudaMemcpyAsync(spread, ds, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, mm->stream));
     }
     MCK(cudaStreamSynchronize(mm->stream));
+    return check_infer(mm);
+}
+
+lbm_status lbm_mlp_set_wait_limit(lbm_mlp* mm, long long cycles) {
+    if (!mm) return mfail(nullptr, LBM_ERR_INVALID_ARG, "mlp is NULL");
+    if (cycles < 0) return mfail(mm, LBM_ERR_INVALID_ARG, "cycles must be >= 0");
+    MCK(cudaStreamSynchronize(mm->stream));
+    mm->wait_limit = cycles ? cycles : TC_WAIT_LIMIT;
+    return LBM_OK;
+}
+
+lbm_status lbm_mlp_set_infer_path(lbm_mlp* mm, int path) {
+    if (!mm) return mfail(nullptr, LBM_ERR_INVALID_ARG, "mlp is NULL");
+    if (path != LBM_MLP_INFER_TENSOR && path != LBM_MLP_INFER_SIMT)
+        return mfail(mm, LBM_ERR_INVALID_ARG, "unknown inference path");
+    MCK(cudaStreamSynchronize(mm->stream));
+    mm->infer_path = path;
     return LBM_OK;
 }
 
 void lbm_mlp_destroy(lbm_mlp* mm) {
     if (!mm) return;
     if (mm->stream) cudaStreamSynchronize(mm->stream);
-    void* p[] = {mm->params, mm->m, mm->v, mm->wt, mm->ws};
+    void* p[] = {mm->params, mm->m, mm->v, mm->wt, mm->tcimg, mm->status, mm->ws};
     for (void* q : p)
         if (q) cudaFree(q);
     delete mm;

@@ -175,6 +175,10 @@ def load():
                                 ctypes.c_uint64]
     L.lbm_mlp_predict.restype = ctypes.c_int
     L.lbm_mlp_predict.argtypes = [c_mlp, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    L.lbm_mlp_set_infer_path.restype = ctypes.c_int
+    L.lbm_mlp_set_infer_path.argtypes = [c_mlp, ctypes.c_int]
+    L.lbm_mlp_set_wait_limit.restype = ctypes.c_int
+    L.lbm_mlp_set_wait_limit.argtypes = [c_mlp, ctypes.c_longlong]
     L.lbm_mlp_destroy.restype = None
     L.lbm_mlp_destroy.argtypes = [c_mlp]
     L.lbm_mlp_last_error.restype = ctypes.c_char_p
@@ -503,6 +507,17 @@ class MLP:
         if st != LBM_OK:
             msg = load().lbm_mlp_last_error(self.h)
             raise LbmError(st, msg.decode() if msg else "")
+
+    INFER_PATHS = {"simt": 0, "tensor": 1}
+
+    def set_infer_path(self, name):
+        """'simt' (FP32 FMAs) or 'tensor' (tcgen05 split products) for
+        forward and predict (lbm_mlp_set_infer_path)."""
+        self._check(load().lbm_mlp_set_infer_path(self.h, self.INFER_PATHS[name]))
+
+    def set_wait_limit(self, cycles):
+        """Longest tensor-core wait in SM cycles (0: default) (lbm_mlp_set_wait_limit)."""
+        self._check(load().lbm_mlp_set_wait_limit(self.h, int(cycles)))
 
     @staticmethod
     def _f32(a, cols):

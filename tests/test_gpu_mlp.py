@@ -62,13 +62,15 @@ def data(n, seed):
     return X, T
 
 
+@pytest.mark.parametrize("path", ["simt", "tensor"])
 @pytest.mark.parametrize("n", [1, 31, 100, 257])
-def test_forward_matches_oracle(lbm, n):
+def test_forward_matches_oracle(lbm, n, path):
     E = 3
     flat, ps = f32_params(members_params(E, 11 + n))
     X, _ = data(n, 5 + n)
     net = lbm.MLP(E)
     try:
+        net.set_infer_path(path)
         net.set_params(flat)
         assert np.array_equal(net.params(), flat)
         Y = net.forward(X)
@@ -139,12 +141,14 @@ def test_adam_minibatch_steps_match_oracle(lbm):
         assert np.abs(got[e] - flat[e]).max() <= 2 * lr * 1.01
 
 
-def test_predict_mean_and_spread(lbm):
+@pytest.mark.parametrize("path", ["simt", "tensor"])
+def test_predict_mean_and_spread(lbm, path):
     E, n = 5, 300
     flat, ps = f32_params(members_params(E, 41))
     X, _ = data(n, 17)
     net = lbm.MLP(E)
     try:
+        net.set_infer_path(path)
         net.set_params(flat)
         mean, spread = net.predict(X)
     finally:
@@ -194,3 +198,50 @@ def test_training_lowers_the_loss(lbm):
         l0 = M.loss(M.unflatten(p0[e]), X.astype(np.float64), T.astype(np.float64))
         l1 = M.loss(M.unflatten(p1[e]), X.astype(np.float64), T.astype(np.float64))
         assert l1 < 0.05 * l0, (e, l0, l1)
+
+
+def test_tensor_path_agrees_with_simt_path_on_a_large_batch(lbm):
+    """65,536 points x 5 members (the size the surrogate is timed on): the
+    tcgen05 split-product path and the FP32 path agree to FP32 level, and
+    sampled rows match the FP64 oracle."""
+    E, n = 5, 65536
+    flat, ps = f32_params(members_params(E, 61))
+    X, _ = data(n, 29)
+    net = lbm.MLP(E)
+    try:
+        net.set_params(flat)
+        net.set_infer_path("simt")
+        Ys = net.forward(X)
+        net.set_infer_path("tensor")
+        Yt = net.forward(X)
+    finally:
+        net.close()
+    scale = np.abs(Ys).max()
+    assert np.abs(Yt - Ys).max() <= 2e-5 * scale
+    rows = np.random.default_rng(3).choice(n, 64, replace=False)
+    for e in range(E):
+        ref, _ = M.forward(ps[e], X[rows].astype(np.float64))
+        assert np.abs(Yt[e][rows] - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+def test_tensor_path_wait_that_runs_out_is_reported(lbm):
+    """A one-cycle limit makes the tensor-core kernel's first wait (on its
+    weight copy) run out: the call fails with LBM_ERR_TIMEOUT, and with the
+    default limit back the ensemble predicts correctly again."""
+    E, n = 2, 500
+    flat, ps = f32_params(members_params(E, 71))
+    X, _ = data(n, 31)
+    net = lbm.MLP(E)
+    try:
+        net.set_params(flat)
+        net.set_infer_path("tensor")
+        net.set_wait_limit(1)
+        with pytest.raises(lbm.LbmError, match="TIMEOUT"):
+            net.forward(X)
+        net.set_wait_limit(0)
+        Y = net.forward(X)
+    finally:
+        net.close()
+    for e in range(E):
+        ref, _ = M.forward(ps[e], X.astype(np.float64))
+        assert np.abs(Y[e] - ref).max() <= 2e-5 * np.abs(ref).max()
