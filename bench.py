@@ -512,7 +512,7 @@ def mlp_kernels(stream_handle, n_infer=65536, n_train=4096, members=5, reps=10):
 
 
 def surrogate_eval(args, stream_handle):
-    """Train the surrogate on solver runs and judge it on held-out runs."""
+    """Train the surrogate on solver runs and evaluate it on held-out runs."""
     import numpy as np
     import torch
 

@@ -90,7 +90,7 @@ def components(rho, solid):
 
 
 def test_coflow_device_drips_at_low_and_jets_at_high_continuous_speed():
-    """The config-3 coaxial device (Sec. III D, Figs. 10-11; 384 long here,
+    """The coaxial co-flow device (Sec. III D, Figs. 10-11; 384 x 96 x 96 here,
     bore w_d = 24).  At u_c = 0.01 the dispersed thread grows from the
     nozzle, necks and pinches off (dripping, Fig. 10(b)): the attached
     thread's volume grows monotonically until the pinch-off, then drops, and
