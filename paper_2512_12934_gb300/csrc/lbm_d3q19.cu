@@ -129,6 +129,8 @@ struct Tile3 {
     static constexpr int NT = TX * TY * TZ;
     static constexpr int MIN_BLOCKS = sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 2 : 3);
 };
+static_assert(HX == RHO_BOX3_X && HY == RHO_BOX3_Y && Tile3<float>::HZ == RHO_BOX3_Z,
+              "the density tensor-copy box must be the FP32 collide tile plus its halo");
 
 template <typename R>
 struct Pair;
@@ -182,7 +184,7 @@ __device__ __forceinline__ long long node_index(const D3Args<S>& a, int x, int y
 // Pull the 19 populations of component k at (x, y, z) (Eq. 2, Eq. B1, Eq. B2).
 // Away from periodic edges the source of direction i is n minus a fixed
 // offset (e_x + e_y pitch + e_z ny pitch); across an edge it is wrapped.
-template <typename S, typename R>
+template <typename S, typename R, bool FAST = true>
 __device__ __forceinline__ void pull(const D3Args<S>& a, int k, int x, int y, int z, uint32_t info, R (&f)[Q]) {
     const S* __restrict__ fin = a.fin + (size_t)k * Q * a.plane;
     const long long n = node_index(a, x, y, z);
@@ -192,6 +194,21 @@ __device__ __forceinline__ void pull(const D3Args<S>& a, int k, int x, int y, in
     // reference density (the writer used the same half-rounded density)
     R ref = 0;
     if constexpr (is_half<S>()) ref = __half2float(a.rref_in[(size_t)k * a.plane + n]);
+    if (FAST && !wrapped && (info & 0x7FFFFu) == 0u) {
+        // no blocked direction, no wrap (most fluid nodes): straight neighbour loads
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            long long src = n;
+            if constexpr (ex_(i) != 0) src -= ex_(i);
+            if constexpr (ey_(i) == 1) src -= sy;
+            if constexpr (ey_(i) == -1) src += sy;
+            if constexpr (ez_(i) == 1) src -= sz;
+            if constexpr (ez_(i) == -1) src += sz;
+            f[i] = (R)ld_pop(fin[(size_t)i * a.plane + src]);
+            if constexpr (is_half<S>()) f[i] += ((R)w36_(i) / (R)36) * ref;
+        });
+        return;
+    }
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         if (info & (1u << i)) {
@@ -430,9 +447,8 @@ __global__ void __launch_bounds__(256, 4) d3q_pull_kernel(D3Args<S> a) {
     if (x >= a.nx || y >= a.ny || z >= a.nz) return;
     const long long n = node_index(a, x, y, z);
     const uint32_t info = a.info[n];
-    if (info & INFO3_SOLID) {  // rho_1 = SOLID_MARK flags a solid site for the force stencil (psi = 0 there)
-        a.rho[n] = (R)SOLID_MARK;
-        a.rho[a.plane + n] = (R)0;
+    if (info & INFO3_SOLID) {  // psi = 0 at solid sites of the force stencil
+        reinterpret_cast<typename Pair<R>::type*>(a.rho)[n] = typename Pair<R>::type{(R)0, (R)0};
         return;
     }
     if ((info >> INFO3_FACE_SHIFT) & 7u) return;  // open-face nodes: d3q_face_pull_kernel
@@ -459,15 +475,17 @@ __global__ void __launch_bounds__(256, 4) d3q_pull_kernel(D3Args<S> a) {
                 }
                 acc += __half2float(fin[(size_t)ii * a.plane + src]);
             });
-            a.rho[(size_t)k * a.plane + n] = __half2float(a.rref_in[(size_t)k * a.plane + n]) + acc;
+            a.rho[2 * n + k] = __half2float(a.rref_in[(size_t)k * a.plane + n]) + acc;
         }
     } else {
+        R r[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             R f[Q];
-            pull<S, R>(a, k, x, y, z, info, f);
-            a.rho[(size_t)k * a.plane + n] = sum19(f);
+            pull<S, R, false>(a, k, x, y, z, info, f);
+            r[k] = sum19(f);
         }
+        reinterpret_cast<typename Pair<R>::type*>(a.rho)[n] = typename Pair<R>::type{r[0], r[1]};
     }
 }
 
@@ -498,15 +516,14 @@ __global__ void __launch_bounds__(128) d3q_face_pull_kernel(D3Args<S> a) {
     pull<S, R>(a, 0, c[0], c[1], c[2], info, f[0]);
     pull<S, R>(a, 1, c[0], c[1], c[2], info, f[1]);
     face_reconstruct<S>(a, fid, c[0], c[1], c[2], info, f);
-    a.rho[n] = sum19(f[0]);
-    a.rho[a.plane + n] = sum19(f[1]);
+    reinterpret_cast<typename Pair<R>::type*>(a.rho)[n] = typename Pair<R>::type{sum19(f[0]), sum19(f[1])};
 }
 
 // ---- kernel B: forces, velocity, collision --------------------------------
 // Resolve a psi / indicator site (Eqs. 10, 11, 24, 25) to a node index:
 // periodic wrap, ghost mirror across open sides, -1 outside a closed side
-// (a solid wall).  Solid nodes inside the grid carry rho_1 = SOLID_MARK, a
-// value no density reaches (the minor component can dip slightly below 0).
+// (a solid wall).  Solid nodes inside the grid carry (0, 0) in the density
+// field: psi = 0 there, as at closed sides.
 template <typename S>
 __device__ __forceinline__ long long site_index(const D3Args<S>& a, int x, int y, int z) {
     int c[3] = {x, y, z};
@@ -582,6 +599,24 @@ __device__ __forceinline__ void stencil_sums(Site site, R (&g1)[3], R (&g2)[3]) 
 }
 
 // sum_e w s(x+e) e of Eq. 11 (geometry only; precomputed per near-solid node)
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Wait for phase `parity` of an mbarrier for at most about a second of SM
+// clock; false if the wait ran out.
+__device__ __forceinline__ bool bar_wait(unsigned long long* bar, unsigned parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(smem_addr(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+}
+
 template <typename S>
 __device__ __forceinline__ void adhesion_vector(const D3Args<S>& a, long long n, uint32_t info,
                                                 typename Store<S>::R (&ad)[3]) {
@@ -640,7 +675,7 @@ template <typename S>
 __device__ __forceinline__ void check_store_u(const D3Args<S>& a, long long n, typename Store<S>::R rt,
                                               const typename Store<S>::R (&u)[3]) {
     if (!(isfinite((float)rt) && isfinite((float)u[0]) && isfinite((float)u[1]) && isfinite((float)u[2])))
-        atomicOr(a.status, 1u);
+        atomicOr(a.status, STATUS3_DIVERGED);
     if (a.umac) {
         a.umac[n] = u[0];
         a.umac[a.plane + n] = u[1];
@@ -658,10 +693,14 @@ __device__ __forceinline__ void check_store_u(const D3Args<S>& a, long long n, t
 // words), FP16 storage 3 of 256 (its decode needs more live values), FP64 1
 // of 256.  Tiles without a fluid node leave before staging.
 template <typename S>
-__global__ void __launch_bounds__(Tile3<S>::NT, Tile3<S>::MIN_BLOCKS) d3q_collide_kernel(D3Args<S> a) {
+__global__ void __launch_bounds__(Tile3<S>::NT, Tile3<S>::MIN_BLOCKS)
+    d3q_collide_kernel(D3Args<S> a, const __grid_constant__ CUtensorMap rho_map, int use_tma) {
     using R = typename Store<S>::R;
     constexpr int TZ = Tile3<S>::TZ, HN = Tile3<S>::HN, NT = Tile3<S>::NT;
-    __shared__ typename Pair<R>::type s_rr[HN];  // (rho_1, rho_2) of the tile and its halo, psi = 0 at solids
+    // (rho_1, rho_2) of the tile and its halo, psi = 0 at solids; 128-byte
+    // aligned: an interior FP32 tile receives it as one tensor copy
+    __shared__ __align__(128) typename Pair<R>::type s_rr[HN];
+    __shared__ __align__(8) unsigned long long s_bar;
     __shared__ __half2 s_ref[is_half<S>() ? HN : 1];  // FP16 storage: the same densities rounded to half
     __shared__ R s_rate[2][Q];  // relaxation rates of both components (indexed by component below)
     // component 0's pulled populations, kept for its collision after
@@ -681,18 +720,42 @@ __global__ void __launch_bounds__(Tile3<S>::NT, Tile3<S>::MIN_BLOCKS) d3q_collid
     // tiles whose halo lies inside the grid need no wrap / mirror / wall resolution
     const bool inner = x0 >= 2 && y0 >= 2 && z0 >= 2 && x0 + TX + 2 <= a.nx && y0 + TY + 2 <= a.ny &&
                        z0 + TZ + 2 <= a.nz;
-    for (int q = tid; q < HN; q += NT) {
-        const int hx = q % HX, hy = (q / HX) % HY, hz = q / (HX * HY);
-        const long long m = inner ? node_index(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz)
-                                  : site_index(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz);
-        typename Pair<R>::type v;
-        v.x = m < 0 ? (R)SOLID_MARK : a.rho[m];
-        v.y = m < 0 ? (R)0 : a.rho[a.plane + m];
-        if (v.x < (R)(0.5 * SOLID_MARK)) v.x = (R)0;
-        s_rr[q] = v;
-        if constexpr (is_half<S>()) s_ref[q] = __floats2half2_rn((float)v.x, (float)v.y);
+    bool staged = false;
+    if constexpr (std::is_same<S, float>::value) {
+        // interior FP32 tile: the (TX+4) x (TY+4) x (TZ+4) box of density
+        // pairs as one TMA copy (x0 - 2 is even: an 8-byte element start on a
+        // 16-byte boundary); the block-uniform test keeps a misaligned
+        // destination on the load path
+        if (use_tma && inner && (smem_addr(s_rr) & 127u) == 0u) {
+            if (tid == 0) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar)) : "memory");
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&s_bar)),
+                             "r"((unsigned)(HN * sizeof(typename Pair<R>::type)))
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], "
+                    "[%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(s_rr)),
+                    "l"(&rho_map), "r"(x0 - 2), "r"(y0 - 2), "r"(z0 - 2), "r"(smem_addr(&s_bar))
+                    : "memory");
+            }
+            __syncthreads();  // the barrier exists before anyone waits on it; s_rate is written
+            if (!bar_wait(&s_bar, 0u) && tid == 0) atomicOr(a.status, STATUS3_TIMEOUT);
+            staged = true;
+        }
     }
-    __syncthreads();
+    if (!staged) {
+        const auto* rp = reinterpret_cast<const typename Pair<R>::type*>(a.rho);
+        for (int q = tid; q < HN; q += NT) {
+            const int hx = q % HX, hy = (q / HX) % HY, hz = q / (HX * HY);
+            const long long m = inner ? node_index(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz)
+                                      : site_index(a, x0 - 2 + hx, y0 - 2 + hy, z0 - 2 + hz);
+            const typename Pair<R>::type v = m < 0 ? typename Pair<R>::type{(R)0, (R)0} : rp[m];
+            s_rr[q] = v;
+            if constexpr (is_half<S>()) s_ref[q] = __floats2half2_rn((float)v.x, (float)v.y);
+        }
+        __syncthreads();
+    }
     if (info & INFO3_SOLID) return;  // solid, or outside the grid
     const int hc = (threadIdx.x + 2) + HX * ((threadIdx.y + 2) + HY * (threadIdx.z + 2));
     auto site = [&](int dx, int dy, int dz) { return s_rr[hc + dx + HX * (dy + HY * dz)]; };
@@ -818,7 +881,7 @@ __global__ void __launch_bounds__(128) d3q_outlet_kernel(D3Args<S> a) {
     const FaceDev3& Fc = a.face[fid];
     if (Fc.kind != FACE3_OUTLET) return;
     const long long n = node_index(a, c[0], c[1], c[2]);
-    const R r1 = a.rho[n], r2 = a.rho[a.plane + n], rt = r1 + r2;
+    const R r1 = a.rho[2 * n], r2 = a.rho[2 * n + 1], rt = r1 + r2;
     const R* Fp = a.FpF + (size_t)slot * 6;
     const R F1[3] = {Fp[0], Fp[1], Fp[2]}, F2[3] = {Fp[3], Fp[4], Fp[5]};
     const R* ff = a.fface + (size_t)slot * 2 * Q;
@@ -841,7 +904,7 @@ __global__ void __launch_bounds__(128) d3q_outlet_kernel(D3Args<S> a) {
         constexpr int i = decltype(I)::value;
         long long m = n;
         if (!(info & (1u << opp_(i)))) m = site_index(a, c[0] + ex_(i), c[1] + ey_(i), c[2] + ez_(i));
-        return half_round(a.rho[(size_t)k * a.plane + m]);
+        return half_round(a.rho[2 * m + k]);
     };
     if constexpr (is_half<S>()) {
         a.rref_out[n] = __float2half_rn(r1);
@@ -969,7 +1032,8 @@ __global__ void __launch_bounds__(256) d3q_mass_kernel(const S* __restrict__ f, 
 }
 
 template <typename S>
-cudaError_t launch_step(const D3Args<S>& a, cudaStream_t st, cudaEvent_t mid_a, cudaEvent_t mid_b) {
+cudaError_t launch_step(const D3Args<S>& a, const CUtensorMap* rho_map, cudaStream_t st, cudaEvent_t mid_a,
+                        cudaEvent_t mid_b) {
     const dim3 blkA(32, 4, 2);
     const dim3 grdA((a.nx + 31) / 32, (a.ny + 3) / 4, (a.nz + 1) / 2);
     const int fblocks = (a.nface_slots + 127) / 128;
@@ -984,7 +1048,8 @@ cudaError_t launch_step(const D3Args<S>& a, cudaStream_t st, cudaEvent_t mid_a, 
     constexpr int TZ = Tile3<S>::TZ;
     const dim3 blkB(TX, TY, TZ);
     const dim3 grdB((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + TZ - 1) / TZ);
-    d3q_collide_kernel<S><<<grdB, blkB, 0, st>>>(a);
+    static const CUtensorMap kNoMap{};
+    d3q_collide_kernel<S><<<grdB, blkB, 0, st>>>(a, rho_map ? *rho_map : kNoMap, rho_map ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (mid_b) cudaEventRecord(mid_b, st);
     if (a.nface_slots > 0) {
@@ -1004,9 +1069,12 @@ cudaError_t launch_mass(const S* f, const uint32_t* info, const typename Real<S>
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step<float>(const D3Args<float>&, cudaStream_t, cudaEvent_t, cudaEvent_t);
-template cudaError_t launch_step<double>(const D3Args<double>&, cudaStream_t, cudaEvent_t, cudaEvent_t);
-template cudaError_t launch_step<__half>(const D3Args<__half>&, cudaStream_t, cudaEvent_t, cudaEvent_t);
+template cudaError_t launch_step<float>(const D3Args<float>&, const CUtensorMap*, cudaStream_t, cudaEvent_t,
+                                          cudaEvent_t);
+template cudaError_t launch_step<double>(const D3Args<double>&, const CUtensorMap*, cudaStream_t, cudaEvent_t,
+                                          cudaEvent_t);
+template cudaError_t launch_step<__half>(const D3Args<__half>&, const CUtensorMap*, cudaStream_t, cudaEvent_t,
+                                          cudaEvent_t);
 template cudaError_t launch_mass<float>(const float*, const uint32_t*, const float*, const __half*, int, int, int,
                                         int, long long, double*, int, cudaStream_t);
 template cudaError_t launch_mass<double>(const double*, const uint32_t*, const double*, const __half*, int, int, int,

@@ -1,6 +1,7 @@
 // D3Q19 kernels: argument block, face descriptors and launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -24,8 +25,12 @@ constexpr uint32_t INFO3_NEAR_SOLID = 1u << 26;
 constexpr uint32_t INFO3_WRAP = 1u << 27;
 
 enum { FACE3_INLET = 1, FACE3_OUTLET = 2 };
-// rho_1 of solid nodes in the density field (read as psi = 0, s = 1)
-constexpr double SOLID_MARK = -1.0e30;
+// status word bits of a D3Q19 step: non-finite result; a bounded wait on a
+// tensor copy that ran out
+constexpr unsigned STATUS3_DIVERGED = 1u, STATUS3_TIMEOUT = 2u;
+// density box of one FP32 collide tile (32 x 4 x 4 nodes) and its 2-node halo,
+// the tensor-copy box of the density field
+constexpr int RHO_BOX3_X = 36, RHO_BOX3_Y = 8, RHO_BOX3_Z = 8;
 // device scalars of the open boundaries (ping-pong per step)
 enum { SC3_LAMBDA = 0, SC3_CHI = 1, SC3_QIN = 2, SC3_QOUT = 3, SC3_UMEAN = 4, SC3_N = 8 };
 
@@ -67,7 +72,7 @@ struct D3Args {
     const S* fin;
     S* fout;
     const uint32_t* info;
-    R* rho;   // [2][plane] component densities of the step
+    R* rho;   // [plane][2] (rho_1, rho_2) of each node for the step, (0, 0) at solids (psi = 0)
     R* umac;  // [3][plane] u^eq of the step (may be null)
     // FP16 storage only: [2][plane] half-rounded density of each node, the
     // reference its pulled populations are decoded with (in: this step's
@@ -95,9 +100,12 @@ struct D3Args {
     R s[2][Q];
 };
 
+// rho_map: tensor map of the density field as 8-byte (rho_1, rho_2) pairs
+// (FP32 contexts; NULL: the collide kernel stages every density box with
+// loads)
 template <typename S>
-cudaError_t launch_step(const D3Args<S>& a, cudaStream_t st, cudaEvent_t mid_a = nullptr,
-                        cudaEvent_t mid_b = nullptr);
+cudaError_t launch_step(const D3Args<S>& a, const CUtensorMap* rho_map, cudaStream_t st,
+                        cudaEvent_t mid_a = nullptr, cudaEvent_t mid_b = nullptr);
 
 // FP64 sums over fluid nodes of each component's populations and the
 // largest |u|^2: partial [nblocks][3].  FP16 storage decodes every

@@ -91,6 +91,10 @@ struct Ctx3 {
     double* flux = nullptr;
     double* scal[2] = {nullptr, nullptr};
     unsigned int* status = nullptr;
+    // FP32: tensor map of the density field as 8-byte (rho_1, rho_2) pairs,
+    // box (36, 8, 8) = one collide tile and its halo
+    CUtensorMap rho_map{};
+    int have_rho_map = 0;
     double* mass_partial = nullptr;
     int mass_blocks = 0;
     double G[3] = {0, 0, 0}, body[3] = {0, 0, 0}, s[2][Q];
@@ -282,15 +286,12 @@ lbm_status upload_state(Ctx3* c, const double* rho_init, const double* u_init) {
         for (int y = 0; y < c->ny; ++y)
             for (int x = 0; x < c->nx; ++x) {
                 const long long h = hidx(c, x, y, z), d = didx(c, x, y, z);
-                if (c->solid[h]) {
-                    rh[d] = T(SOLID_MARK);  // solid marker of the density field (psi = 0 there)
-                    continue;
-                }
+                if (c->solid[h]) continue;  // (0, 0) in the density field: psi = 0 there
                 double u[3];
                 for (int a = 0; a < 3; ++a) u[a] = u_init ? u_init[(size_t)a * N + h] : 0.0;
                 for (int k = 0; k < 2; ++k) {
                     const double r = rho_init[(size_t)k * N + h];
-                    rh[(size_t)k * c->plane + d] = (T)r;
+                    rh[2 * (size_t)d + k] = (T)r;
                     for (int i = 0; i < Q; ++i) fh[((size_t)k * Q + i) * c->plane + d] = host_feq(i, r, u[0], u[1], u[2]);
                 }
                 for (int a = 0; a < 3; ++a) uh[(size_t)a * c->plane + d] = (T)u[a];
@@ -334,10 +335,40 @@ lbm_status upload_state(Ctx3* c, const double* rho_init, const double* u_init) {
     return LBM_OK;
 }
 
+// FP32 contexts: tensor map of the density field ([plane] pairs of floats as
+// 8-byte elements over x, y, z) for the collide kernel's one-copy staging of
+// interior tiles.  Without the driver entry point the kernel stages with
+// loads instead (same values).
+void make_rho_map(Ctx3* c) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    c->have_rho_map = 0;
+    if (c->precision != LBM_FP32) return;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->ny, (cuuint64_t)c->nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * 8, (cuuint64_t)c->pitch * 8 * (cuuint64_t)c->ny};
+    const cuuint32_t box[3] = {(cuuint32_t)RHO_BOX3_X, (cuuint32_t)RHO_BOX3_Y, (cuuint32_t)RHO_BOX3_Z};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(&c->rho_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, c->rho, dims,
+                                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    c->have_rho_map = r == CUDA_SUCCESS ? 1 : 0;
+}
+
 lbm_status check_status3(Ctx3* c) {
     unsigned int st = 0;
     CK3(cudaMemcpyAsync(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
     CK3(cudaStreamSynchronize(c->stream));
+    if (st & STATUS3_TIMEOUT)
+        return fail3(c, nullptr, LBM_ERR_TIMEOUT, "a bounded wait on the density-box tensor copy ran out");
     if (st) return fail3(c, nullptr, LBM_ERR_DIVERGED, "non-finite density or velocity produced");
     return LBM_OK;
 }
@@ -623,6 +654,7 @@ lbm_status create(const lbm_grid* g, const lbm_params* p, const lbm_open_bc* bcs
         destroy(c);
         return fail3(nullptr, err, LBM_ERR_CUDA, msg);
     }
+    make_rho_map(c);
     const lbm_status st = c->sb == 8   ? upload_state<double>(c, rho_init, u_init)
                           : c->sb == 2 ? upload_state<__half>(c, rho_init, u_init)
                                        : upload_state<float>(c, rho_init, u_init);
@@ -652,15 +684,18 @@ lbm_status step(Ctx3* c, int64_t nsteps) {
         if (c->sb == 8) {
             D3Args<double> a;
             fill_args(c, a, true);
-            e = launch_step<double>(a, c->stream, timed ? c->ev[1] : nullptr, timed ? c->ev[2] : nullptr);
+            e = launch_step<double>(a, nullptr, c->stream, timed ? c->ev[1] : nullptr,
+                                 timed ? c->ev[2] : nullptr);
         } else if (c->sb == 2) {
             D3Args<__half> a;
             fill_args(c, a, true);
-            e = launch_step<__half>(a, c->stream, timed ? c->ev[1] : nullptr, timed ? c->ev[2] : nullptr);
+            e = launch_step<__half>(a, nullptr, c->stream, timed ? c->ev[1] : nullptr,
+                                 timed ? c->ev[2] : nullptr);
         } else {
             D3Args<float> a;
             fill_args(c, a, true);
-            e = launch_step<float>(a, c->stream, timed ? c->ev[1] : nullptr, timed ? c->ev[2] : nullptr);
+            e = launch_step<float>(a, c->have_rho_map ? &c->rho_map : nullptr, c->stream, timed ? c->ev[1] : nullptr,
+                                 timed ? c->ev[2] : nullptr);
         }
         if (e != cudaSuccess) return fail3(c, nullptr, LBM_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
         if (timed) {
@@ -716,7 +751,7 @@ static lbm_status macros_impl(Ctx3* c, O* rho, O* u, bool dst_dev) {
             for (int x = 0; x < c->nx; ++x) {
                 const long long h = hidx(c, x, y, z), d = didx(c, x, y, z);
                 const bool s = c->solid[h] != 0;
-                for (int k = 0; k < 2; ++k) ro[(size_t)k * N + h] = s ? O(0) : (O)r[(size_t)k * c->plane + d];
+                for (int k = 0; k < 2; ++k) ro[(size_t)k * N + h] = s ? O(0) : (O)r[2 * (size_t)d + k];
                 for (int a = 0; a < 3; ++a) uo[(size_t)a * N + h] = s ? O(0) : (O)uu[(size_t)a * c->plane + d];
             }
     if (dst_dev) {
