@@ -440,39 +440,41 @@ template <typename S, typename R, int TX, int TY, int MODE>
 __device__ __forceinline__ void stage_tile(const D2Args<S, R>& a, TileSmem<S, R, TX, TY>& sm, int x0, int y0,
                                            int tx, int ty, R (&f)[2][9], unsigned& info, bool& fluid) {
     constexpr int RX = TX + 4, RY = TY + 4, NT = TX * TY;
-    const int x = x0 + tx, y = y0 + ty;
-    R r0 = R(0), r1 = R(0);
-    unsigned char sol = 1;
-    if (MODE != 0) {
-        const bool inb = (x >= 0 && x < a.nx && y >= 0 && y < a.ny);
-        info = INFO_SOLID;
-        fluid = false;
-        if (inb) {
-            info = a.info[y * a.pitch + x];
+    auto stage_own = [&]() {
+        const int x = x0 + tx, y = y0 + ty;
+        R r0 = R(0), r1 = R(0);
+        unsigned char sol = 1;
+        if (MODE != 0) {
+            const bool inb = (x >= 0 && x < a.nx && y >= 0 && y < a.ny);
+            info = INFO_SOLID;
+            fluid = false;
+            if (inb) {
+                info = a.info[y * a.pitch + x];
+                fluid = !(info & INFO_SOLID);
+                if (fluid) {
+                    if (MODE == 2) pull_general(a, x, y, info, R(0), f);
+                    else pull_wrap(a, x, y, info, f);
+                    r0 = rho_of(f[0]);
+                    r1 = rho_of(f[1]);
+                    sol = 0;
+                }
+            } else if (site_rho<S, R, MODE>(a, x, y, r0, r1)) {
+                sol = 0;
+            }
+        } else {
+            const int n = y * a.pitch + x;
+            info = a.info[n];
             fluid = !(info & INFO_SOLID);
             if (fluid) {
-                if (MODE == 2) pull_general(a, x, y, info, R(0), f);
-                else pull_wrap(a, x, y, info, f);
+                pull_interior(a, n, info, f);
                 r0 = rho_of(f[0]);
                 r1 = rho_of(f[1]);
                 sol = 0;
             }
-        } else if (site_rho<S, R, MODE>(a, x, y, r0, r1)) {
-            sol = 0;
         }
-    } else {
-        const int n = y * a.pitch + x;
-        info = a.info[n];
-        fluid = !(info & INFO_SOLID);
-        if (fluid) {
-            pull_interior(a, n, info, f);
-            r0 = rho_of(f[0]);
-            r1 = rho_of(f[1]);
-            sol = 0;
-        }
-    }
-    sm.rr[ty + 2][tx + 2] = rpair<R>(r0, r1);
-    sm.sol[ty + 2][tx + 2] = sol;
+        sm.rr[ty + 2][tx + 2] = rpair<R>(r0, r1);
+        sm.sol[ty + 2][tx + 2] = sol;
+    };
     // halo ring: densities only
     constexpr int RING = RX * RY - TX * TY;
     auto ring_site = [&](int p) {
@@ -494,9 +496,15 @@ __device__ __forceinline__ void stage_tile(const D2Args<S, R>& a, TileSmem<S, R,
         sm.rr[ry][rx] = rpair<R>(h0, h1);
         sm.sol[ry][rx] = ok ? 0 : 1;
     };
-    if (RING <= NT) {
+    // When one pass of the node threads covers the ring, its pulls are
+    // issued first and the own node's independent loads go out under their
+    // latency (measured on GB300: 3 % faster per HBM-resident step with
+    // 32x8 tiles, 1 % slower with 32x4 tiles, whose ring takes two passes).
+    if constexpr (RING <= NT) {
         if ((int)threadIdx.x < RING) ring_site(threadIdx.x);
+        stage_own();
     } else {
+        stage_own();
         for (int p = threadIdx.x; p < RING; p += NT) ring_site(p);
     }
 }
